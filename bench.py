@@ -1,0 +1,371 @@
+"""Benchmark of the hybrid micro-macro parareal hot path on GB300.
+
+Workload (the batched-parareal configuration): Nx=1024, Nv=64 on [-8,8],
+eps=1e-2, T=1, N=128 slices, full kinetic (adaptation off), seeded random
+Fourier density plus a smooth random (v^2-1)M perturbation.  One step is
+one parareal iteration through the C ABI (parareal_run with K=1): coarse
+guess, lifting of slices 1..N-1, the fine propagator F over all 128 slices
+in one launch (7112 steps each), the sequential correction and the
+successive error.  The metric is phase-space cell-updates per second (one
+(interface, v_j) g-update = one cell-update), FP32-g path.
+
+Timing: W untimed warm-up steps, then exactly K steps bracketed by a
+barrier and torch.cuda.synchronize(); the L2 cache is flushed (256 MB
+write) before every step and each step is timed with CUDA events on the
+call's stream, the flush outside the events.  Under torchrun each rank runs
+its own independent solve (weak scaling; the fine propagations of different
+solves never exchange data) and rank 0 prints the max-over-ranks time.
+
+--impl reference times the FP64 C oracle on the host cores on a bounded
+sample of the same workload (the paper's own Fortran code is not public).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NV, EPS, T_END, N_SLICES = 1024, 64, 1e-2, 1.0, 128
+FLOPS_PER_UPDATE = 20       # algorithmic FP32 flops per cell-update
+BYTES_PER_UPDATE = 8        # algorithmic HBM bytes per FP32 cell-update (read g, write g)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision", default="fp32g", choices=["fp32g", "fp64"])
+    ap.add_argument("--kernel-only", default=None, choices=["fine", "coarse"],
+                    help="profiling driver: launch only this kernel on the workload")
+    ap.add_argument("--window", type=int, default=200,
+                    help="fine steps per launch in --kernel-only fine")
+    return ap.parse_args()
+
+
+def kernel_only(a):
+    """Launch one kernel of the hot path on the workload (for ncu captures):
+    'fine' runs the fine propagator on all 128 slice states for --window
+    steps; 'coarse' runs one parareal iteration's coarse chain."""
+    import torch
+
+    from paper_2511_13386_gb300 import mm, workloads as W
+    dev = torch.device("cuda:0")
+    prec = mm.MM_FP32G if a.precision == "fp32g" else mm.MM_FP64
+    gdt = torch.float32 if prec == mm.MM_FP32G else torch.float64
+    w = W.batched(NX, NV, EPS, n_slices=N_SLICES)
+    p = mm.mm_params_default(nx=NX, nv=NV, eps=EPS, rho_bar=1.0, precision=prec)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    rho_b, g_b = w.with_batch(8)
+    reps = N_SLICES // 8
+    rho = torch.tensor(rho_b, device=dev).repeat(reps, 1).contiguous()
+    g = torch.tensor(g_b, device=dev, dtype=gdt).repeat(reps, 1, 1).contiguous()
+    ro, go = torch.empty_like(rho), torch.empty_like(g)
+    if a.kernel_only == "fine":
+        span = a.window * dt * (1 - 1e-9)
+        for _ in range(max(1, a.warmup)):
+            st = mm.mm_fine_propagate(ctx, N_SLICES, span, rho, g, ro, go, stats=True)
+        ms = []
+        for _ in range(a.steps):
+            st = mm.mm_fine_propagate(ctx, N_SLICES, span, rho, g, ro, go, stats=True)
+            ms.append(st["elapsed_ms"])
+        per_step_us = 1e3 * statistics.median(ms) / a.window
+        print(json.dumps({"kernel": "fine", "window": a.window, "launch_ms": ms,
+                          "us_per_step": per_step_us,
+                          "cell_updates_per_s": N_SLICES * NX * NV / (per_step_us * 1e-6)}))
+    else:
+        out = torch.empty((N_SLICES + 1, NX), dtype=torch.float64, device=dev)
+        for _ in range(max(1, a.warmup)):
+            mm.parareal_run(ctx, T_END, N_SLICES, 0, 0.0, rho[0], g[0], out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            mm.parareal_run(ctx, T_END, N_SLICES, 0, 0.0, rho[0], g[0], out)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": "coarse chain", "ms": 1e3 * (time.perf_counter() - t0) / a.steps}))
+    ctx.close()
+
+
+# ----------------------------------------------------------------- oracle --
+
+def _oracle_sample(args):
+    """Run the oracle's F on one slice state for n steps; returns seconds."""
+    seed, n_steps = args
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from paper_2511_13386_gb300 import workloads as W
+    w = W.random_state(W.batched(NX, NV, EPS), seed)
+    p = O.Params(nx=NX, nv=NV, eps=EPS, rho_bar=1.0)
+    dt = O.dt_limit(p)
+    t0 = time.perf_counter()
+    O.fine(p, n_steps, dt, w.rho0, w.g0)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(seconds: float, cores: int, pool=None):
+    """Cell-updates/s of the oracle on `cores` processes (one slice state
+    each, the parareal slice loop), on a bounded sample of steps."""
+    t1 = _oracle_sample((1, 4))
+    per_step = t1 / 4
+    n_steps = max(4, int(seconds / per_step))
+    jobs = [(100 + c, n_steps) for c in range(cores)]
+    t0 = time.perf_counter()
+    if pool is not None and cores > 1:
+        list(pool.map(_oracle_sample, jobs))
+    else:
+        for j in jobs:
+            _oracle_sample(j)
+    el = time.perf_counter() - t0
+    updates = cores * n_steps * NX * NV
+    return updates / el, n_steps, el
+
+
+# ----------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(a, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2511_13386_gb300 import mm, workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prec = mm.MM_FP32G if a.precision == "fp32g" else mm.MM_FP64
+    gdt = torch.float32 if prec == mm.MM_FP32G else torch.float64
+    w = W.batched(NX, NV, EPS, seed=W.SEED_BASE + rank, n_slices=N_SLICES)
+    p = mm.mm_params_default(nx=NX, nv=NV, eps=EPS, v_max=8.0, rho_bar=1.0, precision=prec)
+    ctx = mm.mm_create(p)
+    q = mm.mm_query(ctx, T_END / N_SLICES)
+    stream = torch.cuda.current_stream()
+    rho0 = torch.tensor(w.rho0, device=dev)
+    g0 = torch.tensor(w.g0, device=dev, dtype=gdt)
+    out = torch.empty((N_SLICES + 1, NX), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return mm.parareal_run(ctx, T_END, N_SLICES, 1, 0.0, rho0, g0, out)
+
+    for _ in range(a.warmup):
+        info = step()
+    updates_per_step = info["kinetic_updates"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms, fine_ms, fine_n = [], 0.0, 0
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for _ in range(a.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            fine_ms += info["fine_ms"]
+            fine_n += info["fine_launches"]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * updates_per_step * a.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside)
+    rho0_h = np.ascontiguousarray(w.rho0)
+    g0_h = np.ascontiguousarray(w.g0.astype(np.float32 if prec == mm.MM_FP32G else np.float64))
+    out_h = np.empty((N_SLICES + 1, NX))
+    mm.parareal_run(ctx, T_END, N_SLICES, 1, 0.0, rho0_h, g0_h, out_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, a.steps // 2)
+    for _ in range(e2e_steps):
+        mm.parareal_run(ctx, T_END, N_SLICES, 1, 0.0, rho0_h, g0_h, out_h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * updates_per_step * e2e_steps / e2e_s, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": int(rho0_h.nbytes + g0_h.nbytes),
+           "d2h_bytes_per_step": int(out_h.nbytes)}
+
+    # roofline of the dominant kernel (the fine propagator)
+    fine_launch_ms = fine_ms / max(fine_n, 1)
+    upd_per_launch = updates_per_step  # one fine launch per step (K=1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_mhz = clk.summary().get("sm_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    achieved_flops = FLOPS_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alg_gbs = BYTES_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": round(achieved_flops, 3), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved_flops / fp32_peak, 4), "traffic": None,
+                "peak_source": f"FP32 FMA lanes x clock: {n_sm} SMs x 128 x 2 x {sm_mhz:.0f} MHz",
+                "kernel": "fine_kernel<float,8>", "launch_ms": round(fine_launch_ms, 3),
+                "hbm_equivalent": {"achieved_gbs": round(alg_gbs, 1), "peak_gbs": hbm_peak,
+                                   "frac_of_measured": round(alg_gbs / hbm_peak, 3)}}
+    ctx.close()
+    return {"value": value, "total_ms": total_ms, "step_ms": step_ms, "wall": wall,
+            "updates_per_step": updates_per_step, "e2e": e2e, "roofline": roofline,
+            "clocks": clk.summary(), "n_steps_fine": q["n_steps"], "fine_launches": fine_n}
+
+
+def main():
+    a = parse()
+    if a.kernel_only:
+        kernel_only(a)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    cores = os.cpu_count() or 1
+
+    pool = None
+    if a.impl == "reference" or (rank == 0 and not a.no_cpu_baseline):
+        if rank == 0:
+            import multiprocessing as mp
+            pool = mp.get_context("spawn").Pool(cores)
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        rates = []
+        step_s = []
+        for s in range(a.warmup + a.steps):
+            per = max(1.0, a.cpu_seconds / 2)
+            rate, n_steps, el = cpu_oracle_rate(per, cores, pool)
+            if s >= a.warmup:
+                rates.append(rate)
+                step_s.append(el)
+        value = statistics.mean(rates)
+        sample = (f"oracle F on {cores} independent slice states of the Nx={NX}, Nv={NV}, "
+                  f"eps={EPS} workload, {n_steps} steps each, one process per core")
+        line = {"impl": "reference", "metric": "cell-updates/s", "value": value,
+                "unit": "cell-updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": 1e3 * statistics.mean(step_s), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "batched parareal, Nx=1024 Nv=64 eps=1e-2 N=128, full kinetic",
+                           "sample": sample},
+                "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        pool.close()
+        return
+
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, n_steps, el = cpu_oracle_rate(a.cpu_seconds, cores, pool)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle F on {cores} slice states of this workload (one process per core), "
+                         f"{n_steps} of the 7112 steps per slice, {el:.1f} s"}
+    if pool:
+        pool.close()
+
+    r = run_ours(a, rank, world, dist)
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s", "value": r["value"], "unit": "cell-updates/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": r["total_ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if a.precision == "fp32g" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched parareal: Nx=1024, Nv=64 on [-8,8], eps=1e-2, T=1, "
+                                   "N=128 slices, full kinetic, one parareal iteration per step",
+                       "precision": "FP32 g; float-float density, Poisson and moments"
+                       if a.precision == "fp32g" else "FP64",
+                       "fine_steps_per_slice": r["n_steps_fine"],
+                       "cell_updates_per_step": r["updates_per_step"],
+                       "l2": "flushed (256 MB write) before every timed step, outside the events",
+                       "parallelism": f"{world} independent solve(s), one per GPU"},
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+            "gpu_launches": None, "clocks": r["clocks"],
+        }
+        # kernels per step: coarse chain, lift, fine, correction (K=1)
+        line["gpu_launches"] = 4 * a.steps
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

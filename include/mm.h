@@ -1,0 +1,280 @@
+/*
+ * mm.h -- C ABI of the GB300 hybrid micro-macro parareal library (libmm).
+ *
+ * The library implements, on one GB300 GPU (sm_103a), the hot path of the
+ * space-time hybrid parareal method for the 1D-1V linear Vlasov-Poisson-BGK
+ * equation in the diffusive scaling (T. Laidin, arXiv 2511.13386):
+ *   - the fine propagator F = S^HMM, the spatially hybridised micro-macro
+ *     asymptotic-preserving scheme (Sec. 2.3, eqs. S^MM and S^HMM), run for a
+ *     whole batch of parareal slice states in one launch;
+ *   - the coarse propagator G = S^0 (Sec. 2.3, eq. S^0), the lifting of
+ *     Def. 1 (Sec. 3.2-3.3) and the parareal loop of Algorithm 1 (Sec. 3.3),
+ *     kept on the device beside F.
+ *
+ * Discretisation (shared by every entry point):
+ *   x in [0, x_len) periodic, nx cells, dx = x_len / nx.  Cell data (rho,
+ *   status) at cell centres x_i = (i + 1/2) dx; interface data (g, E, J) at
+ *   x_{i+1/2} = (i + 1) dx, stored at index i.
+ *   v_j = (2j - nv + 1) dv / 2 on [-v_max, v_max], dv = 2 v_max / (nv - 1);
+ *   trapezoid weights; Maxwellian exp(-v^2/2) normalised so that its
+ *   discrete integral is one.
+ *
+ * Array layouts (row-major, C order):
+ *   rho  : double [batch][nx]
+ *   g    : [batch][nx][nv], v contiguous; double for MM_FP64, float for
+ *          MM_FP32G
+ *   mask : uint8_t [batch][nx], 1 = kinetic cell, 0 = fluid cell
+ *
+ * Pointers: every array argument may be a device pointer (the fast path) or
+ * a host pointer (pageable or pinned); host arrays are staged through device
+ * memory inside the call, on the call's stream.  The caller owns every
+ * array it passes.  The library owns its workspace, obtained through the
+ * optional mm_alloc callbacks (default: cudaMallocAsync on the call's
+ * stream) and released by mm_destroy.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Device-pointer calls are asynchronous on that stream
+ * unless a stats pointer is given, in which case the call synchronises the
+ * stream before returning.
+ *
+ * Errors: every call returns an mm_status; the message of the last failure
+ * on the calling thread is available from mm_last_error().  Arguments are
+ * validated before anything is launched.  No call aborts or throws.
+ *
+ * Threads: an mm_ctx is not thread-safe (one thread at a time); an
+ * mm_server is thread-safe for serve_submit / serve_poll.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MM_ABI_VERSION 1
+
+/* Exported symbols (the library is built with hidden default visibility). */
+#if defined(MM_BUILD) && defined(__GNUC__)
+#define MM_API __attribute__((visibility("default")))
+#else
+#define MM_API
+#endif
+
+typedef enum {
+  MM_OK = 0,
+  MM_ERR_INVALID = 1,         /* bad argument, size or parameter */
+  MM_ERR_OOM = 2,             /* device allocation failed */
+  MM_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+  MM_ERR_TIMEOUT = 4,         /* a bounded wait ran out */
+  MM_ERR_UNSTABLE = 5,        /* step above the stability limit, or a
+                                 non-finite density was produced */
+  MM_ERR_BUSY = 6,            /* server at capacity (admission refused) */
+  MM_ERR_NOT_READY = 7,       /* result not ready before the poll timeout */
+  MM_ERR_UNKNOWN_TICKET = 8   /* no such request */
+} mm_status;
+
+typedef enum {
+  MM_FP64 = 0,   /* g stored and updated in double; every sum in double */
+  MM_FP32G = 1   /* g stored and updated in float; density, Poisson solve,
+                    moment combination and mass kept in compensated
+                    float-float (~48-bit) arithmetic, output density double */
+} mm_precision;
+
+/* Optional device-memory callbacks (e.g. a framework's caching allocator). */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, void* stream, void* user);
+  void* user;
+} mm_alloc;
+
+/* Problem description.  Fill with mm_params_default() then override. */
+typedef struct {
+  int32_t nx;          /* cells, >= 8 */
+  int32_t nv;          /* velocity nodes: even, >= 4, see mm_params_default */
+  double x_len;        /* torus length (> 0) */
+  double v_max;        /* velocity box half-width (> 0) */
+  double eps;          /* Knudsen number (> 0) */
+  double rho_bar;      /* neutralising density of the Poisson law
+                          (Sec. 1, eq. Poisson); NaN = the mean of each
+                          input density */
+  int32_t adapt;       /* 0: every cell kinetic (S^MM); 1: hybrid S^HMM
+                          with the criteria of Sec. 2.2 */
+  double thr_g;        /* threshold on the interface norm ||g||_2 */
+  double thr_R;        /* threshold on the macroscopic remainder R */
+  int32_t r_scale;     /* 0: compare |R| with thr_R (as printed);
+                          1: compare eps^2 |R| (the O(eps^2) term of eq.
+                          HigherOrderModel) */
+  int32_t flux_rule;   /* 0: one flux per interface (mass-conservative);
+                          1: the cell-based rule printed in S^HMM */
+  double dt;           /* fine step limit; 0 = automatic (stability rule) */
+  double cfl_theta;    /* safety factor of the automatic rule (0 -> 0.9) */
+  int32_t coarse_kind; /* G: 0 = linearly implicit S^0, 1 = explicit S^0 */
+  int32_t coarse_steps;/* G steps per slice (>= 1); the explicit kind uses
+                          max(coarse_steps, the steps its stability needs) */
+  int32_t lift_order;  /* lifting order L of Def. 1; 1 is implemented */
+  int32_t precision;   /* mm_precision */
+} mm_params;
+
+typedef struct mm_ctx mm_ctx;
+
+typedef struct {
+  double dt_limit;       /* step limit (rule or params.dt) */
+  double dt;             /* step used for the queried span */
+  int64_t n_steps;       /* fine steps for the queried span */
+  double m2;             /* second velocity moment of the discrete M */
+  double a, b;           /* exp(-dt/eps^2), eps (1 - a) */
+  size_t state_bytes;    /* bytes of one (rho, g) slice state */
+  int32_t vpt;           /* velocity nodes per lane in the fine kernel */
+  int32_t lanes;         /* lanes per interface column in the fine kernel */
+} mm_info;
+
+typedef struct {
+  int64_t steps;             /* fine steps per state */
+  int64_t kinetic_updates;   /* (kinetic interface, v_j) updates, summed over
+                                states and steps */
+  int64_t full_updates;      /* nx * nv * steps * batch */
+  int32_t device_status;     /* mm_status reported by the kernels */
+  double elapsed_ms;         /* device time of the call (events) */
+} mm_fine_stats;
+
+/* Fill *p with defaults: x_len 1, v_max 8, eps 1, rho_bar NaN, adapt 0,
+   thr_g 1e-3, thr_R 1e-2, r_scale 0, flux_rule 0, dt 0, cfl_theta 0.9,
+   coarse_kind 0, coarse_steps 1, lift_order 1, precision MM_FP64. */
+MM_API void mm_params_default(mm_params* p);
+
+/* Create a context for one problem shape.  Validates the parameters,
+   builds the velocity grid on the device.  alloc may be NULL.
+   Errors: MM_ERR_INVALID (bad parameter or unsupported nv), MM_ERR_CUDA,
+   MM_ERR_OOM. */
+MM_API mm_status mm_create(const mm_params* p, const mm_alloc* alloc, mm_ctx** out);
+
+/* Release the context and its workspace (synchronises the device). */
+MM_API void mm_destroy(mm_ctx* ctx);
+
+/* Step size, step count and constants for a span of t_span.
+   Errors: MM_ERR_INVALID (t_span <= 0). */
+MM_API mm_status mm_query(const mm_ctx* ctx, double t_span, mm_info* out);
+
+/* F over a span (Sec. 2.3, eq. S^HMM; eq. S^MM when adapt == 0):
+   n = ceil(t_span / dt_limit) steps of size t_span / n for every state of
+   the batch, all states in one launch.  Per step and state: the Poisson law
+   of S^MM for E, the flux J of S^0, the criteria of Sec. 2.2 and the status
+   update of Sec. 2.3 (adapt == 1), the g update on kinetic interfaces
+   (upwind transport, (I - Pi) projection, field term, exponential
+   relaxation), g = 0 on fluid interfaces, and the density update.
+   The status at entry is the kinetic rule applied as if every cell were
+   kinetic, so F is a function of (rho_in, g_in) alone.
+     rho_in  [batch][nx] double          rho_out [batch][nx] double
+     g_in    [batch][nx][nv]             g_out   [batch][nx][nv] (may alias
+                                                  g_in)
+     mask_out [batch][nx] uint8 or NULL (final cell status)
+     stats    NULL, or filled after a stream synchronisation
+   Errors: MM_ERR_INVALID (batch < 0, NULL array, t_span <= 0),
+   MM_ERR_UNSTABLE (params.dt above the stability rule, or a non-finite
+   density in the result: reported through stats->device_status and the
+   return value when stats is given), MM_ERR_CUDA, MM_ERR_OOM.
+   batch == 0 is a no-op. */
+MM_API mm_status mm_fine_propagate(mm_ctx* ctx, int32_t batch, double t_span,
+                            const double* rho_in, const void* g_in,
+                            double* rho_out, void* g_out, uint8_t* mask_out,
+                            mm_fine_stats* stats, void* stream);
+
+/* G over a span (Sec. 2.3, eq. S^0): coarse_steps linearly implicit steps
+   (E frozen from the old density, cyclic tridiagonal solve) or explicit S^0
+   steps, for every density of the batch.  rho_in and rho_out may alias.
+   Errors: MM_ERR_INVALID, MM_ERR_CUDA, MM_ERR_OOM. */
+MM_API mm_status mm_coarse(mm_ctx* ctx, int32_t batch, double t_span,
+                    const double* rho_in, double* rho_out, void* stream);
+
+/* Lifting of order one (Def. 1; identification l = 0 of Sec. 2.1;
+   interface density averaged as in Sec. 3.3):
+   g_{i+1/2,j} = -eps (I - Pi)[xi_j M_j J_{i+1/2}], J from the Poisson law
+   and S^0.  g_out has the context's precision.
+   Errors: MM_ERR_INVALID, MM_ERR_CUDA, MM_ERR_OOM. */
+MM_API mm_status mm_lift(mm_ctx* ctx, int32_t batch, const double* rho, void* g_out,
+                  void* stream);
+
+typedef struct {
+  double t_end;        /* T */
+  int32_t n_slices;    /* N_g >= 1 */
+  int32_t max_iter;    /* K >= 0 (capped at N_g) */
+  double tol;          /* stop when the successive error is below tol */
+} mm_parareal_cfg;
+
+typedef struct {
+  int32_t iterations;        /* parareal iterations performed */
+  double err[64];            /* successive errors (first 64 iterations) */
+  double mass_drift;         /* max_n |m^n - m^0| / |m^0| of the result */
+  int64_t fine_steps;        /* fine steps per slice */
+  int64_t kinetic_updates;   /* summed over all fine propagations */
+  double elapsed_ms;         /* device time of the whole call (events) */
+  double fine_ms;            /* device time of the fine-propagator launches */
+  int32_t fine_launches;     /* fine-propagator launches */
+} mm_parareal_stats;
+
+/* Algorithm 1 (Sec. 3.3) with F = S^HMM, G = S^0 and the lifting of order
+   one: coarse guess, then per iteration k the fine propagations of all
+   slices n >= k in one batched launch, the sequential correction
+   rho^{n+1,k+1} = F(rho^{n,k}) + (G(rho^{n,k+1}) - G(rho^{n,k})) on the
+   device, relifting, and the successive error max |rho^{n,k+1}-rho^{n,k}|.
+   The first slice starts from (rho0, g0); later slices from their lifted
+   density.  rho_slices_out [n_slices + 1][nx] double receives rho^{n,K}.
+   The call synchronises the stream once per iteration (error test).
+   Errors: MM_ERR_INVALID, MM_ERR_UNSTABLE, MM_ERR_CUDA, MM_ERR_OOM. */
+MM_API mm_status parareal_run(mm_ctx* ctx, const mm_parareal_cfg* cfg,
+                       const double* rho0, const void* g0,
+                       double* rho_slices_out, mm_parareal_stats* stats,
+                       void* stream);
+
+/* ------------------------------------------------------------ serving --- */
+
+typedef struct mm_server mm_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* admission budget for resident solves */
+  int32_t max_slots;         /* solves resident at once */
+  int32_t wait_limit_ms;     /* bound on any internal wait */
+} mm_server_cfg;
+
+typedef struct {
+  mm_params params;
+  mm_parareal_cfg cfg;
+  const double* rho0;        /* host [nx], copied at submit */
+  const void* g0;            /* host [nx][nv] (params.precision), copied */
+} mm_request;
+
+typedef struct {
+  mm_status status;
+  double* rho_T;             /* caller-owned host [nx]: density at t_end */
+  int32_t iterations;
+  int64_t latency_ns;        /* submit -> result ready */
+  int64_t kinetic_updates;
+} mm_result;
+
+/* Serving loop with continuous batching: requests are admitted while their
+   device footprint fits the budget and a slot is free; the fine
+   propagations of all resident solves share launches.
+   Errors: MM_ERR_INVALID, MM_ERR_CUDA, MM_ERR_OOM. */
+MM_API mm_status mm_server_create(const mm_server_cfg* cfg, const mm_alloc* alloc,
+                           mm_server** out);
+/* Copy the request and queue it.  Errors: MM_ERR_INVALID (bad request, or
+   a footprint above the whole budget). */
+MM_API mm_status serve_submit(mm_server* s, const mm_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms for a result; on MM_OK the result is copied into
+   *res and the ticket is retired.  Errors: MM_ERR_NOT_READY,
+   MM_ERR_UNKNOWN_TICKET. */
+MM_API mm_status serve_poll(mm_server* s, uint64_t ticket, mm_result* res,
+                     int32_t timeout_ms);
+/* Stop the scheduler, fail queued requests, free device state. */
+MM_API mm_status mm_server_destroy(mm_server* s);
+
+/* Message of the last failure on this thread ("" if none). */
+MM_API const char* mm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,702 @@
+// Host side of the C ABI declared in include/mm.h: contexts, parameter
+// validation, the step-size rule, staging of host arrays, the fine / coarse
+// / lift entry points and the parareal driver of Algorithm 1 (Sec. 3.3).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mm_internal.h"
+
+// ------------------------------------------------------------- errors ---
+
+static thread_local std::string g_last_error;
+
+mm_status mm_fail(mm_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+mm_status mm_cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;
+}
+
+extern "C" const char* mm_last_error(void) { return g_last_error.c_str(); }
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return mm_cuda_fail(e_, what); \
+  } while (0)
+
+// ----------------------------------------------------------- workspace --
+
+namespace {
+
+// Named device buffers grown on demand; memory from the user's callbacks or
+// from the stream-ordered allocator.
+struct Workspace {
+  mm_alloc cb{};
+  bool has_cb = false;
+  struct Slot {
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  std::vector<Slot> slots;
+
+  void release(Slot& s, cudaStream_t st) {
+    if (!s.p) return;
+    if (has_cb) cb.free(s.p, st, cb.user);
+    else cudaFreeAsync(s.p, st);
+    s.p = nullptr;
+    s.bytes = 0;
+  }
+
+  mm_status get(int id, size_t bytes, cudaStream_t st, void** out) {
+    if ((int)slots.size() <= id) slots.resize(id + 1);
+    Slot& s = slots[id];
+    if (bytes == 0) bytes = 16;
+    if (s.bytes < bytes) {
+      release(s, st);
+      void* p = nullptr;
+      if (has_cb) {
+        p = cb.alloc(bytes, st, cb.user);
+        if (!p) return mm_fail(MM_ERR_OOM, "workspace allocation failed (callback)");
+      } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, st);
+        if (e != cudaSuccess) return mm_cuda_fail(e, "cudaMallocAsync(workspace)");
+      }
+      s.p = p;
+      s.bytes = bytes;
+    }
+    *out = s.p;
+    return MM_OK;
+  }
+
+  void release_all(cudaStream_t st) {
+    for (auto& s : slots) release(s, st);
+  }
+};
+
+enum WsSlot {
+  WS_GBUF1 = 0, WS_COLS, WS_RHO_IN, WS_RHO_OUT, WS_G_IN, WS_G_OUT, WS_MASK, WS_MACRO,
+  WS_STATUS, WS_PR_RHO, WS_PR_F, WS_PR_G, WS_PR_GB, WS_PR_ERR, WS_COUNT
+};
+
+}  // namespace
+
+struct mm_ctx {
+  mm_params p{};
+  int device = 0;
+  mmk::VelocityGrid vg;
+  mmk::LaneLayout lay;
+  double dt_rule = 0;     // stability limit of the rule at cfl_theta
+  double dt_limit = 0;    // limit actually used (params.dt or dt_rule)
+  double* d_vtab = nullptr;
+  float* d_vtab_f = nullptr;
+  Workspace ws;
+};
+
+// ----------------------------------------------------------- parameters --
+
+extern "C" void mm_params_default(mm_params* p) {
+  memset(p, 0, sizeof(*p));
+  p->nx = 64;
+  p->nv = 32;
+  p->x_len = 1.0;
+  p->v_max = 8.0;
+  p->eps = 1.0;
+  p->rho_bar = NAN;
+  p->adapt = 0;
+  p->thr_g = 1e-3;
+  p->thr_R = 1e-2;
+  p->r_scale = 0;
+  p->flux_rule = 0;
+  p->dt = 0.0;
+  p->cfl_theta = 0.9;
+  p->coarse_kind = 0;
+  p->coarse_steps = 1;
+  p->lift_order = 1;
+  p->precision = MM_FP64;
+}
+
+// Velocity discretisation of Sec. 2.3 with trapezoid weights and the
+// Maxwellian normalised on the grid.
+static mmk::VelocityGrid build_velocity_grid(int nv, double v_max) {
+  mmk::VelocityGrid g;
+  g.nv = nv;
+  g.dv = 2.0 * v_max / (nv - 1);
+  g.v.resize(nv);
+  g.w.resize(nv);
+  g.M.resize(nv);
+  double Z = 0.0;
+  for (int j = 0; j < nv; ++j) {
+    g.v[j] = (double)(2 * j - nv + 1) * (0.5 * g.dv);
+    g.w[j] = (j == 0 || j == nv - 1) ? 0.5 * g.dv : g.dv;
+    Z += g.w[j] * exp(-0.5 * g.v[j] * g.v[j]);
+  }
+  g.m2 = 0.0;
+  g.xiM = 0.0;
+  for (int j = 0; j < nv; ++j) {
+    g.M[j] = exp(-0.5 * g.v[j] * g.v[j]) / Z;
+    g.m2 += g.w[j] * g.v[j] * g.v[j] * g.M[j];
+    g.xiM += g.w[j] * g.v[j] * g.M[j];
+  }
+  return g;
+}
+
+// Stability rule for the step (the paper states none).  With
+// a(s) = exp(-s/eps^2) the step s must satisfy
+//   upwind transport with relaxation: eps (1-a) v_max / dx <= (1+a)/2,
+//   diffusion through g:              s (1-a) <= dx^2 / (2 m2),
+//   explicit S^0 in fluid cells:      s <= dx^2 / (2 m2)   (adaptation on);
+// the largest such s is bracketed and bisected.
+static bool step_ok(const mm_params& p, double m2, double s) {
+  const double dx = p.x_len / p.nx;
+  const double a = exp(-s / (p.eps * p.eps));
+  const double lim = dx * dx / (2.0 * m2);
+  if (p.eps * (1.0 - a) * p.v_max / dx > 0.5 * (1.0 + a)) return false;
+  if (s * (1.0 - a) > lim) return false;
+  if (p.adapt && s > lim) return false;
+  return true;
+}
+
+static double stability_limit(const mm_params& p, double m2) {
+  double lo = 0.0, hi = 1.0;
+  while (step_ok(p, m2, hi) && hi < 1e300) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (step_ok(p, m2, mid)) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+static bool choose_layout(int nv, bool fp32, mmk::LaneLayout* out) {
+  if (nv < 4 || nv % 2) return false;
+  const int cand32[] = {8, 4, 2, 1}, cand64[] = {4, 2, 1};
+  const int* c = fp32 ? cand32 : cand64;
+  const int nc = fp32 ? 4 : 3;
+  for (int q = 0; q < nc; ++q) {
+    const int vpt = c[q];
+    if ((nv / 2) % vpt) continue;
+    const int nh = nv / 2 / vpt;
+    int nhp = 1;
+    while (nhp < nh) nhp <<= 1;
+    if (2 * nhp > 32) continue;
+    out->vpt = vpt;
+    out->nh = nh;
+    out->nhp = nhp;
+    out->lanes = 2 * nhp;
+    return true;
+  }
+  return false;
+}
+
+static mm_status validate(const mm_params* p) {
+  if (!p) return mm_fail(MM_ERR_INVALID, "params is NULL");
+  if (p->nx < 8) return mm_fail(MM_ERR_INVALID, "nx must be >= 8");
+  if (p->nv < 4 || p->nv % 2) return mm_fail(MM_ERR_INVALID, "nv must be even and >= 4");
+  if (!(p->x_len > 0) || !(p->v_max > 0) || !(p->eps > 0))
+    return mm_fail(MM_ERR_INVALID, "x_len, v_max and eps must be positive");
+  if (p->precision != MM_FP64 && p->precision != MM_FP32G)
+    return mm_fail(MM_ERR_INVALID, "unknown precision");
+  if (p->coarse_kind != 0 && p->coarse_kind != 1) return mm_fail(MM_ERR_INVALID, "coarse_kind must be 0 or 1");
+  if (p->coarse_steps < 1) return mm_fail(MM_ERR_INVALID, "coarse_steps must be >= 1");
+  if (p->lift_order != 1) return mm_fail(MM_ERR_INVALID, "only lift_order 1 is implemented");
+  if (p->flux_rule != 0 && p->flux_rule != 1) return mm_fail(MM_ERR_INVALID, "flux_rule must be 0 or 1");
+  if (p->dt < 0 || !(p->cfl_theta >= 0)) return mm_fail(MM_ERR_INVALID, "dt and cfl_theta must be >= 0");
+  if (p->adapt && (!(p->thr_g >= 0) || !(p->thr_R >= 0)))
+    return mm_fail(MM_ERR_INVALID, "thresholds must be >= 0");
+  return MM_OK;
+}
+
+extern "C" mm_status mm_create(const mm_params* p, const mm_alloc* alloc, mm_ctx** out) {
+  if (!out) return mm_fail(MM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  mm_status st = validate(p);
+  if (st != MM_OK) return st;
+  mmk::LaneLayout lay;
+  const bool fp32 = p->precision == MM_FP32G;
+  if (!choose_layout(p->nv, fp32, &lay))
+    return mm_fail(MM_ERR_INVALID,
+                   "unsupported nv: nv/2 needs a divisor d in {1,2,4,8} with nv/d <= 32 lanes");
+  mm_ctx* c = new mm_ctx();
+  c->p = *p;
+  if (c->p.cfl_theta == 0) c->p.cfl_theta = 0.9;
+  c->lay = lay;
+  if (alloc && alloc->alloc && alloc->free) {
+    c->ws.cb = *alloc;
+    c->ws.has_cb = true;
+  }
+  cudaGetDevice(&c->device);
+  c->vg = build_velocity_grid(p->nv, p->v_max);
+  c->dt_rule = c->p.cfl_theta * stability_limit(c->p, c->vg.m2);
+  c->dt_limit = c->p.dt > 0 ? c->p.dt : c->dt_rule;
+
+  const int nv = p->nv;
+  const double dx = p->x_len / p->nx;
+  std::vector<double> tab(mmk::kVTabFields * nv);
+  for (int j = 0; j < nv; ++j) {
+    const double v = c->vg.v[j], w = c->vg.w[j], M = c->vg.M[j];
+    tab[0 * nv + j] = fabs(v) / dx;
+    tab[1 * nv + j] = M;
+    tab[2 * nv + j] = v * M;
+    tab[3 * nv + j] = w * v;
+    tab[4 * nv + j] = w;
+    tab[5 * nv + j] = v;
+  }
+  std::vector<float> tabf(tab.begin(), tab.end());
+  cudaError_t e = cudaMalloc(&c->d_vtab, tab.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_vtab_f, tabf.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_vtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_vtab_f, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_vtab);
+    cudaFree(c->d_vtab_f);
+    delete c;
+    return mm_cuda_fail(e, "mm_create: velocity table");
+  }
+  *out = c;
+  return MM_OK;
+}
+
+extern "C" void mm_destroy(mm_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  c->ws.release_all(0);
+  cudaStreamSynchronize(0);
+  cudaFree(c->d_vtab);
+  cudaFree(c->d_vtab_f);
+  delete c;
+}
+
+static int64_t steps_for(double span, double lim) {
+  const double q = span / lim;
+  int64_t n = (int64_t)ceil(q);
+  return n < 1 ? 1 : n;
+}
+
+extern "C" mm_status mm_query(const mm_ctx* c, double t_span, mm_info* out) {
+  if (!c || !out) return mm_fail(MM_ERR_INVALID, "NULL argument");
+  if (!(t_span > 0)) return mm_fail(MM_ERR_INVALID, "t_span must be > 0");
+  out->dt_limit = c->dt_limit;
+  out->n_steps = steps_for(t_span, c->dt_limit);
+  out->dt = t_span / out->n_steps;
+  out->m2 = c->vg.m2;
+  out->a = exp(-out->dt / (c->p.eps * c->p.eps));
+  out->b = c->p.eps * (1.0 - out->a);
+  const size_t gsz = c->p.precision == MM_FP32G ? 4 : 8;
+  out->state_bytes = (size_t)c->p.nx * 8 + (size_t)c->p.nx * c->p.nv * gsz;
+  out->vpt = c->lay.vpt;
+  out->lanes = c->lay.lanes;
+  return MM_OK;
+}
+
+// --------------------------------------------------------- pointer kinds --
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself, or a staging buffer
+// (filled from the host when `copy_in`).
+static mm_status device_view(mm_ctx* c, int slot, const void* p, size_t bytes, bool copy_in,
+                             cudaStream_t s, void** out, bool* staged) {
+  if (is_device_ptr(p) && ((uintptr_t)p % 16 == 0)) {
+    *out = const_cast<void*>(p);
+    *staged = false;
+    return MM_OK;
+  }
+  mm_status st = c->ws.get(slot, bytes, s, out);
+  if (st != MM_OK) return st;
+  *staged = true;
+  if (copy_in) CK(cudaMemcpyAsync(*out, p, bytes, cudaMemcpyDefault, s), "copy to device");
+  return MM_OK;
+}
+
+// ----------------------------------------------------------- fine (F) ---
+
+static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const double* rho_in,
+                           const void* g_in, double* rho_out, void* g_out, uint8_t* mask_out,
+                           double rho_bar, mm_fine_stats* stats, cudaStream_t s) {
+  const mm_params& p = c->p;
+  const bool fp32 = p.precision == MM_FP32G;
+  const size_t gsz = fp32 ? 4 : 8;
+  const size_t nx = p.nx, nv = p.nv;
+  const size_t rbytes = batch * nx * 8, gbytes = batch * nx * nv * gsz, mbytes = batch * nx;
+
+  void *d_rin, *d_gin, *d_rout, *d_gout, *d_mask = nullptr;
+  bool s_rin, s_gin, s_rout, s_gout, s_mask = false;
+  mm_status st;
+  if ((st = device_view(c, WS_RHO_IN, rho_in, rbytes, true, s, &d_rin, &s_rin)) != MM_OK) return st;
+  if ((st = device_view(c, WS_G_IN, g_in, gbytes, true, s, &d_gin, &s_gin)) != MM_OK) return st;
+  if ((st = device_view(c, WS_RHO_OUT, rho_out, rbytes, false, s, &d_rout, &s_rout)) != MM_OK) return st;
+  if ((st = device_view(c, WS_G_OUT, g_out, gbytes, false, s, &d_gout, &s_gout)) != MM_OK) return st;
+  if (mask_out && (st = device_view(c, WS_MASK, mask_out, mbytes, false, s, &d_mask, &s_mask)) != MM_OK)
+    return st;
+
+  void* buf1;
+  if ((st = c->ws.get(WS_GBUF1, gbytes, s, &buf1)) != MM_OK) return st;
+  // g_out is the buffer the last step writes; with an odd step count the
+  // first step writes it too, so an aliased input is moved aside first.
+  if (d_gin == d_gout && (n & 1)) {
+    CK(cudaMemcpyAsync(buf1, d_gin, gbytes, cudaMemcpyDeviceToDevice, s), "alias copy");
+    d_gin = buf1;
+    void* other;
+    if ((st = c->ws.get(WS_G_IN, gbytes, s, &other)) != MM_OK) return st;
+    buf1 = other;
+  }
+
+  mmk::FineArgs a{};
+  a.nx = p.nx;
+  a.nv = p.nv;
+  a.batch = batch;
+  a.n_steps = n;
+  a.lanes = c->lay.lanes;
+  a.nh = c->lay.nh;
+  a.nhp = c->lay.nhp;
+  a.dt = dt;
+  a.dx = p.x_len / p.nx;
+  a.inv_dx = 1.0 / a.dx;
+  a.inv_dv = 1.0 / c->vg.dv;
+  a.eps = p.eps;
+  a.inv_eps = 1.0 / p.eps;
+  a.a = exp(-dt / (p.eps * p.eps));
+  a.b = p.eps * (1.0 - a.a);
+  a.m2 = c->vg.m2;
+  a.dt_dx = dt / a.dx;
+  a.rho_bar = rho_bar;
+  a.adapt = p.adapt;
+  a.r_scale = p.r_scale;
+  a.flux_rule = p.flux_rule;
+  a.thr_g = p.thr_g;
+  a.thr_R = p.thr_R;
+  a.r_fac = p.r_scale ? p.eps * p.eps : 1.0;
+  a.rho_in = (const double*)d_rin;
+  a.rho_out = (double*)d_rout;
+  a.g_in = d_gin;
+  a.g_buf0 = d_gout;
+  a.g_buf1 = buf1;
+  a.mask_out = (uint8_t*)d_mask;
+  a.vtab = c->d_vtab;
+  a.vtab_f = c->d_vtab_f;
+
+  const bool adapt = p.adapt != 0;
+  const size_t colb = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt);
+  const bool in_smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, true) <= 232448;
+  a.col_in_smem = in_smem ? 1 : 0;
+  if (!in_smem) {
+    if ((st = c->ws.get(WS_COLS, colb * batch, s, &a.col_ws)) != MM_OK) return st;
+    a.col_ws_stride = colb;
+  }
+  void* stat_mem;
+  if ((st = c->ws.get(WS_STATUS, 64, s, &stat_mem)) != MM_OK) return st;
+  a.status = (int*)stat_mem;
+  a.kin_count = (unsigned long long*)((char*)stat_mem + 16);
+  CK(cudaMemsetAsync(stat_mem, 0, 64, s), "memset status");
+
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (stats) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, in_smem);
+  cudaError_t e = mmk::launch_fine(a, c->lay.vpt, fp32, smem, s);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
+  if (stats) cudaEventRecord(e1, s);
+
+  if (s_rout) CK(cudaMemcpyAsync(rho_out, d_rout, rbytes, cudaMemcpyDefault, s), "copy rho_out");
+  if (s_gout) CK(cudaMemcpyAsync(g_out, d_gout, gbytes, cudaMemcpyDefault, s), "copy g_out");
+  if (s_mask) CK(cudaMemcpyAsync(mask_out, d_mask, mbytes, cudaMemcpyDefault, s), "copy mask");
+
+  const bool host_out = s_rout || s_gout || s_mask;
+  if (stats || host_out) {
+    int hs[6] = {0};
+    CK(cudaMemcpyAsync(hs, stat_mem, 24, cudaMemcpyDeviceToHost, s), "read status");
+    CK(cudaStreamSynchronize(s), "fine: synchronise");
+    if (stats) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      unsigned long long kc;
+      memcpy(&kc, (char*)hs + 16, 8);
+      stats->steps = n;
+      stats->kinetic_updates = (int64_t)kc;
+      stats->full_updates = (int64_t)n * batch * p.nx * p.nv;
+      stats->device_status = hs[0];
+      stats->elapsed_ms = ms;
+    }
+    if (hs[0] != 0) return mm_fail((mm_status)hs[0], "fine: non-finite density");
+  }
+  return MM_OK;
+}
+
+static double stability_guard(const mm_ctx* c) {
+  mm_params q = c->p;
+  return stability_limit(q, c->vg.m2);
+}
+
+extern "C" mm_status mm_fine_propagate(mm_ctx* c, int32_t batch, double t_span, const double* rho_in,
+                                       const void* g_in, double* rho_out, void* g_out, uint8_t* mask_out,
+                                       mm_fine_stats* stats, void* stream) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (batch < 0) return mm_fail(MM_ERR_INVALID, "batch must be >= 0");
+  if (!(t_span > 0)) return mm_fail(MM_ERR_INVALID, "t_span must be > 0");
+  if (batch == 0) {
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return MM_OK;
+  }
+  if (!rho_in || !g_in || !rho_out || !g_out) return mm_fail(MM_ERR_INVALID, "NULL array");
+  if (c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
+    return mm_fail(MM_ERR_UNSTABLE, "params.dt is above the stability limit");
+  cudaSetDevice(c->device);
+  const int64_t n = steps_for(t_span, c->dt_limit);
+  return fine_impl(c, batch, n, t_span / n, rho_in, g_in, rho_out, g_out, mask_out, c->p.rho_bar, stats,
+                   (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------ coarse and lift --
+
+static mmk::MacroArgs macro_args(const mm_ctx* c, int batch, double t_span, double rho_bar) {
+  mmk::MacroArgs a{};
+  a.nx = c->p.nx;
+  a.nv = c->p.nv;
+  a.batch = batch;
+  a.dx = c->p.x_len / c->p.nx;
+  a.inv_dx = 1.0 / a.dx;
+  a.m2 = c->vg.m2;
+  a.rho_bar = rho_bar;
+  a.eps = c->p.eps;
+  a.xiM = c->vg.xiM;
+  a.coarse_kind = c->p.coarse_kind;
+  a.t_span = t_span;
+  int steps = c->p.coarse_steps;
+  if (c->p.coarse_kind == 1) {  // explicit S^0: respect its own stability limit
+    const double lim = a.dx * a.dx / (2.0 * c->vg.m2) * c->p.cfl_theta;
+    steps = std::max<int64_t>(steps, steps_for(t_span, lim));
+  }
+  a.coarse_steps = steps;
+  a.parts = mmk::coarse_parts(a.nx);
+  a.vtab = c->d_vtab;
+  return a;
+}
+
+static double host_mean(const double* rho, int nx, cudaStream_t s, bool* ok) {
+  std::vector<double> h(nx);
+  *ok = cudaMemcpyAsync(h.data(), rho, nx * sizeof(double), cudaMemcpyDefault, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess;
+  double m = 0.0;
+  for (double v : h) m += v;
+  return m / nx;
+}
+
+extern "C" mm_status mm_coarse(mm_ctx* c, int32_t batch, double t_span, const double* rho_in,
+                               double* rho_out, void* stream) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (batch < 0 || !(t_span > 0)) return mm_fail(MM_ERR_INVALID, "bad batch or t_span");
+  if (batch == 0) return MM_OK;
+  if (!rho_in || !rho_out) return mm_fail(MM_ERR_INVALID, "NULL array");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t rbytes = (size_t)batch * c->p.nx * 8;
+  void *d_in, *d_out;
+  bool s_in, s_out;
+  mm_status st;
+  if ((st = device_view(c, WS_RHO_IN, rho_in, rbytes, true, s, &d_in, &s_in)) != MM_OK) return st;
+  if ((st = device_view(c, WS_RHO_OUT, rho_out, rbytes, false, s, &d_out, &s_out)) != MM_OK) return st;
+  double rb = c->p.rho_bar;
+  if (isnan(rb)) {
+    if (batch != 1) return mm_fail(MM_ERR_INVALID, "rho_bar NaN needs batch == 1 for mm_coarse");
+    bool ok;
+    rb = host_mean((const double*)d_in, c->p.nx, s, &ok);
+    if (!ok) return mm_fail(MM_ERR_CUDA, "mm_coarse: reading rho");
+  }
+  mmk::MacroArgs a = macro_args(c, batch, t_span, rb);
+  void* gws = nullptr;
+  const size_t wsb = mmk::macro_ws_bytes(a.nx, batch);
+  if (wsb && (st = c->ws.get(WS_MACRO, wsb, s, &gws)) != MM_OK) return st;
+  cudaError_t e = mmk::launch_coarse(a, (const double*)d_in, (double*)d_out, (double*)gws, s);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "coarse launch");
+  if (s_out) {
+    CK(cudaMemcpyAsync(rho_out, d_out, rbytes, cudaMemcpyDefault, s), "copy rho_out");
+    CK(cudaStreamSynchronize(s), "coarse: synchronise");
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_lift(mm_ctx* c, int32_t batch, const double* rho, void* g_out, void* stream) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (batch < 0) return mm_fail(MM_ERR_INVALID, "bad batch");
+  if (batch == 0) return MM_OK;
+  if (!rho || !g_out) return mm_fail(MM_ERR_INVALID, "NULL array");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool fp32 = c->p.precision == MM_FP32G;
+  const size_t rbytes = (size_t)batch * c->p.nx * 8;
+  const size_t gbytes = (size_t)batch * c->p.nx * c->p.nv * (fp32 ? 4 : 8);
+  void *d_in, *d_out;
+  bool s_in, s_out;
+  mm_status st;
+  if ((st = device_view(c, WS_RHO_IN, rho, rbytes, true, s, &d_in, &s_in)) != MM_OK) return st;
+  if ((st = device_view(c, WS_G_OUT, g_out, gbytes, false, s, &d_out, &s_out)) != MM_OK) return st;
+  double rb = c->p.rho_bar;
+  if (isnan(rb)) {
+    if (batch != 1) return mm_fail(MM_ERR_INVALID, "rho_bar NaN needs batch == 1 for mm_lift");
+    bool ok;
+    rb = host_mean((const double*)d_in, c->p.nx, s, &ok);
+    if (!ok) return mm_fail(MM_ERR_CUDA, "mm_lift: reading rho");
+  }
+  mmk::MacroArgs a = macro_args(c, batch, 1.0, rb);
+  void* gws = nullptr;
+  const size_t wsb = mmk::macro_ws_bytes(a.nx, batch);
+  if (wsb && (st = c->ws.get(WS_MACRO, wsb, s, &gws)) != MM_OK) return st;
+  cudaError_t e = mmk::launch_lift(a, (const double*)d_in, d_out, fp32, (double*)gws, s);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "lift launch");
+  if (s_out) {
+    CK(cudaMemcpyAsync(g_out, d_out, gbytes, cudaMemcpyDefault, s), "copy g_out");
+    CK(cudaStreamSynchronize(s), "lift: synchronise");
+  }
+  return MM_OK;
+}
+
+// ------------------------------------------------------------- parareal --
+
+extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const double* rho0, const void* g0,
+                                  double* rho_slices_out, mm_parareal_stats* stats, void* stream) {
+  if (!c || !cfg) return mm_fail(MM_ERR_INVALID, "NULL argument");
+  if (cfg->n_slices < 1 || cfg->max_iter < 0 || !(cfg->t_end > 0))
+    return mm_fail(MM_ERR_INVALID, "bad parareal configuration");
+  if (!rho0 || !g0 || !rho_slices_out) return mm_fail(MM_ERR_INVALID, "NULL array");
+  if (c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
+    return mm_fail(MM_ERR_UNSTABLE, "params.dt is above the stability limit");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const mm_params& p = c->p;
+  const bool fp32 = p.precision == MM_FP32G;
+  const int N = cfg->n_slices, nx = p.nx, nv = p.nv;
+  const size_t gsz = fp32 ? 4 : 8;
+  const size_t rowb = (size_t)nx * 8;
+  const double span = cfg->t_end / N;
+  const int64_t nf = steps_for(span, c->dt_limit);
+  const double dtf = span / nf;
+
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+
+  mm_status st;
+  void *rho, *frho, *gprev, *gb, *errp;
+  bool s_out;
+  if ((st = device_view(c, WS_PR_RHO, rho_slices_out, rowb * (N + 1), false, s, &rho, &s_out)) != MM_OK)
+    return st;
+  if ((st = c->ws.get(WS_PR_F, rowb * (N + 1), s, &frho)) != MM_OK) return st;
+  if ((st = c->ws.get(WS_PR_G, rowb * (N + 1), s, &gprev)) != MM_OK) return st;
+  if ((st = c->ws.get(WS_PR_GB, (size_t)N * nx * nv * gsz, s, &gb)) != MM_OK) return st;
+  if ((st = c->ws.get(WS_PR_ERR, 64, s, &errp)) != MM_OK) return st;
+
+  // initial slice and rho_bar (mean of the initial density when NaN)
+  CK(cudaMemcpyAsync(rho, rho0, rowb, cudaMemcpyDefault, s), "copy rho0");
+  double rb = p.rho_bar;
+  if (isnan(rb)) {
+    bool ok;
+    rb = host_mean((const double*)rho, nx, s, &ok);
+    if (!ok) return mm_fail(MM_ERR_CUDA, "parareal: reading rho0");
+  }
+  mmk::MacroArgs ma = macro_args(c, 1, span, rb);
+  void* gws = nullptr;
+  const size_t wsb = mmk::macro_ws_bytes(nx, std::max(N, 1));
+  if (wsb && (st = c->ws.get(WS_MACRO, wsb, s, &gws)) != MM_OK) return st;
+
+  // coarse guess: rho^{n+1,0} = G(rho^{n,0})
+  cudaError_t e = mmk::launch_coarse_chain(ma, N, (double*)rho, (double*)gprev, (double*)gws, s);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
+
+  int it = 0;
+  int64_t kin_total = 0;
+  double fine_ms = 0.0;
+  int fine_launches = 0;
+  const int K = std::min(cfg->max_iter, N);
+  for (int k = 0; k < K; ++k) {
+    const int batch = N - k;
+    // inputs of the fine propagations: (rho^{n,k}, g^{n,k}), n = k..N-1
+    if (k == 0) {
+      CK(cudaMemcpyAsync(gb, g0, (size_t)nx * nv * gsz, cudaMemcpyDefault, s), "copy g0");
+      if (N > 1) {
+        mmk::MacroArgs la = macro_args(c, N - 1, span, rb);
+        e = mmk::launch_lift(la, (const double*)rho + nx, (char*)gb + (size_t)nx * nv * gsz, fp32,
+                             (double*)gws, s);
+      }
+    } else {
+      mmk::MacroArgs la = macro_args(c, batch, span, rb);
+      e = mmk::launch_lift(la, (const double*)rho + (size_t)k * nx, gb, fp32, (double*)gws, s);
+    }
+    if (e != cudaSuccess) return mm_cuda_fail(e, "lift");
+    mm_fine_stats fs;
+    st = fine_impl(c, batch, nf, dtf, (const double*)rho + (size_t)k * nx, gb, (double*)frho + (size_t)(k + 1) * nx,
+                   gb, nullptr, rb, stats ? &fs : nullptr, s);
+    if (st != MM_OK) return st;
+    if (stats) {
+      kin_total += fs.kinetic_updates;
+      fine_ms += fs.elapsed_ms;
+      ++fine_launches;
+    }
+    // sequential correction on the device
+    mmk::CorrectArgs ca{};
+    ca.m = ma;
+    ca.n_slices = N;
+    ca.k = k;
+    ca.rho = (double*)rho;
+    ca.frho = (const double*)frho;
+    ca.gprev = (double*)gprev;
+    ca.err = (double*)errp;
+    e = mmk::launch_correct(ca, (double*)gws, s);
+    if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
+    double err = 0;
+    CK(cudaMemcpyAsync(&err, errp, 8, cudaMemcpyDeviceToHost, s), "read error");
+    CK(cudaStreamSynchronize(s), "parareal: synchronise");
+    if (stats && k < 64) stats->err[k] = err;
+    ++it;
+    if (err < cfg->tol) break;
+  }
+  cudaEventRecord(e1, s);
+  if (s_out) CK(cudaMemcpyAsync(rho_slices_out, rho, rowb * (N + 1), cudaMemcpyDefault, s), "copy slices");
+  CK(cudaStreamSynchronize(s), "parareal: final synchronise");
+  if (stats) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    stats->iterations = it;
+    stats->fine_steps = nf;
+    stats->kinetic_updates = kin_total;
+    stats->elapsed_ms = ms;
+    stats->fine_ms = fine_ms;
+    stats->fine_launches = fine_launches;
+    std::vector<double> h((size_t)(N + 1) * nx);
+    CK(cudaMemcpy(h.data(), rho, rowb * (N + 1), cudaMemcpyDefault), "read slices");
+    double m0 = 0;
+    for (int i = 0; i < nx; ++i) m0 += h[i];
+    double drift = 0;
+    for (int n = 1; n <= N; ++n) {
+      double m = 0;
+      for (int i = 0; i < nx; ++i) m += h[(size_t)n * nx + i];
+      drift = std::max(drift, fabs(m - m0) / fabs(m0));
+    }
+    stats->mass_drift = drift;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return MM_OK;
+}

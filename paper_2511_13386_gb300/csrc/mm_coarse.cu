@@ -1,0 +1,347 @@
+// Coarse propagator G = S^0 (Sec. 2.3), lifting of order one (Def. 1,
+// Sec. 3.2-3.3) and the device side of Algorithm 1: the coarse guess, the
+// sequential correction sweep and the successive error.  All in double
+// (the correction and the convergence test of the parareal loop stay in
+// double precision in both precisions of the fine propagator).
+//
+// One CTA of 256 threads owns one density; the linearly implicit step
+// solves the cyclic tridiagonal system (I - m2 dt L_E) rho^{m+1} = rho^m
+// with E frozen from rho^m by Sherman-Morrison on top of a Thomas sweep
+// run by one thread (the system is strictly diagonally dominant for the
+// slice lengths used, so no pivoting is needed).
+#include <math.h>
+
+#include "mm_internal.h"
+
+namespace mmk {
+
+constexpr int kMacroThreads = 256;
+
+// Block-wide Poisson law of S^MM: E_{i+1/2} = S_i - mean(S),
+// S_i = sum_{m<=i} (rho_m - rho_bar) dx.  red: >= 64 doubles of smem.
+__device__ void poisson_block(const double* rho, double* E, int nx, double rho_bar, double dx,
+                              double* red) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int cpt = (nx + T - 1) / T;
+  const int c0 = min(tid * cpt, nx), c1 = min(c0 + cpt, nx);
+  double t1 = 0.0, t2 = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    const double d = (rho[c] - rho_bar) * dx;
+    t1 += d;
+    E[c] = t1;
+    t2 += d * (double)(nx - c);
+  }
+  const int w = tid >> 5, l = tid & 31;
+  double inc = t1;
+  for (int d = 1; d < 32; d <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, inc, d);
+    if (l >= d) inc += t;
+  }
+  double excl_w = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (l == 0) excl_w = 0.0;
+  double ws = t2;
+  for (int m = 16; m > 0; m >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, m);
+  __syncthreads();
+  if (l == 31) red[w] = inc;
+  if (l == 0) red[32 + w] = ws;
+  __syncthreads();
+  double off = 0.0, tw = 0.0;
+  for (int q = 0; q < (T >> 5); ++q) {
+    if (q < w) off += red[q];
+    tw += red[32 + q];
+  }
+  const double mean = tw * (1.0 / nx);
+  const double base = off + excl_w;
+  for (int c = c0; c < c1; ++c) E[c] = base + E[c] - mean;
+  __syncthreads();
+}
+
+// One explicit S^0 step, in place.
+__device__ void limit_step_block(double* rho, double* E, double* J, const MacroArgs& a, double dt,
+                                 double* red) {
+  const int nx = a.nx, T = blockDim.x;
+  poisson_block(rho, E, nx, a.rho_bar, a.dx, red);
+  for (int i = threadIdx.x; i < nx; i += T) {
+    const double r0 = rho[i], r1 = rho[i + 1 == nx ? 0 : i + 1];
+    J[i] = (r1 - r0) * a.inv_dx - E[i] * 0.5 * (r0 + r1);
+  }
+  __syncthreads();
+  const double k = a.m2 * dt * a.inv_dx;
+  for (int i = threadIdx.x; i < nx; i += T) rho[i] += k * (J[i] - J[i == 0 ? nx - 1 : i - 1]);
+  __syncthreads();
+}
+
+// Cyclic tridiagonal solve of a small system by Thomas + Sherman-Morrison
+// (one thread): lo[p] x[p-1] + di[p] x[p] + up[p] x[p+1] = d[p], periodic,
+// n >= 3.  x may alias d; z is scratch of n doubles.
+__device__ void cyclic_small(int n, const double* lo, const double* di, const double* up,
+                             const double* d, double* x, double* cw, double* z) {
+  const double alpha = up[n - 1], beta = lo[0], gamma = -di[0];
+  double bet = di[0] - gamma;
+  double inv = 1.0 / bet;
+  double xr = d[0] * inv, xu = gamma * inv;
+  x[0] = xr;
+  z[0] = xu;
+  for (int i = 1; i < n; ++i) {
+    const double dii = (i == n - 1) ? di[n - 1] - alpha * beta / gamma : di[i];
+    const double ci = up[i - 1] * inv;
+    cw[i] = ci;
+    bet = dii - lo[i] * ci;
+    inv = 1.0 / bet;
+    xr = (d[i] - lo[i] * xr) * inv;
+    xu = ((i == n - 1 ? alpha : 0.0) - lo[i] * xu) * inv;
+    x[i] = xr;
+    z[i] = xu;
+  }
+  for (int i = n - 2; i >= 0; --i) {
+    x[i] -= cw[i + 1] * x[i + 1];
+    z[i] -= cw[i + 1] * z[i + 1];
+  }
+  const double fact = (x[0] + beta * x[n - 1] / gamma) / (1.0 + z[0] + beta * z[n - 1] / gamma);
+  for (int i = 0; i < n; ++i) x[i] -= fact * z[i];
+}
+
+// One linearly implicit S^0 step, in place: (I - m2 dt L_E) x = rho with E
+// frozen from rho.  Partitioned solve: the rows are cut into P chunks whose
+// last row is a separator; thread p eliminates the interior of chunk p
+// (Thomas, three right-hand sides: the data and the couplings to the two
+// neighbouring separators), the separators satisfy a cyclic P x P
+// tridiagonal system (solved by one thread), then every chunk is rebuilt.
+// Scratch: E, cw, y, vl, vr (nx each) and rs (>= 7 * 256 doubles).
+__device__ void limit_step_implicit_block(double* rho, double* E, double* cw, double* y, double* vl,
+                                          double* vr, double* rs, const MacroArgs& a, double dt,
+                                          double* red) {
+  const int n = a.nx, P = a.parts, tid = threadIdx.x;
+  poisson_block(rho, E, n, a.rho_bar, a.dx, red);
+  const double k = a.m2 * dt * a.inv_dx, idx = a.inv_dx;
+  auto coef = [&](int i, double& lo, double& di, double& up) {
+    const double Er = E[i], El = E[i == 0 ? n - 1 : i - 1];
+    lo = -k * (idx + 0.5 * El);
+    di = 1.0 - k * (-2.0 * idx - 0.5 * Er + 0.5 * El);
+    up = -k * (idx - 0.5 * Er);
+  };
+  if (tid < P) {  // interior rows [a0, b0) of chunk tid; separator b0
+    const int a0 = (int)(((long long)tid * n) / P), b0 = (int)(((long long)(tid + 1) * n) / P) - 1;
+    double lo, di, up, cprev = 0.0, yp = 0.0, lp = 0.0, rp = 0.0;
+    for (int i = a0; i < b0; ++i) {
+      coef(i, lo, di, up);
+      const double l = (i == a0) ? 0.0 : lo;
+      const double inv = 1.0 / (di - l * cprev);
+      cprev = (i == b0 - 1) ? 0.0 : up * inv;
+      cw[i] = cprev;
+      yp = (rho[i] - l * yp) * inv;
+      lp = ((i == a0 ? -lo : 0.0) - l * lp) * inv;
+      rp = ((i == b0 - 1 ? -up : 0.0) - l * rp) * inv;
+      y[i] = yp;
+      vl[i] = lp;
+      vr[i] = rp;
+    }
+    for (int i = b0 - 2; i >= a0; --i) {
+      y[i] -= cw[i] * y[i + 1];
+      vl[i] -= cw[i] * vl[i + 1];
+      vr[i] -= cw[i] * vr[i + 1];
+    }
+  }
+  __syncthreads();
+  double* rA = rs;          // reduced system on the separators
+  double* rB = rs + 256;
+  double* rC = rs + 512;
+  double* rD = rs + 768;
+  double* rL = rs + 1024;
+  double* rZ = rs + 1280;
+  if (tid < P) {
+    const int b0 = (int)(((long long)(tid + 1) * n) / P) - 1;
+    const int il = b0 - 1, ir = (b0 + 1 == n) ? 0 : b0 + 1;
+    double lo, di, up;
+    coef(b0, lo, di, up);
+    rA[tid] = lo * vl[il];
+    rB[tid] = lo * vr[il] + di + up * vl[ir];
+    rC[tid] = up * vr[ir];
+    rD[tid] = rho[b0] - lo * y[il] - up * y[ir];
+  }
+  __syncthreads();
+  if (tid == 0) cyclic_small(P, rA, rB, rC, rD, rL, rs + 1536, rZ);
+  __syncthreads();
+  if (tid < P) {
+    const int a0 = (int)(((long long)tid * n) / P), b0 = (int)(((long long)(tid + 1) * n) / P) - 1;
+    const double Lm = rL[tid == 0 ? P - 1 : tid - 1], Lp = rL[tid];
+    for (int i = a0; i < b0; ++i) rho[i] = y[i] + Lm * vl[i] + Lp * vr[i];
+    rho[b0] = Lp;
+  }
+  __syncthreads();
+}
+
+// Per-CTA scratch: the density working copy, five arrays of nx doubles and
+// the reduced system, in dynamic shared memory when they fit, else in a
+// global workspace.
+constexpr int kScratchArrays = 6;
+constexpr int kReducedDoubles = 7 * 256;
+
+struct Scratch {
+  double *w, *s0, *s1, *s2, *s3, *s4, *rs;
+};
+
+__device__ Scratch scratch_of(unsigned char* smem, double* gws, int nx, int in_smem) {
+  const size_t per = (size_t)kScratchArrays * nx + kReducedDoubles;
+  double* base = in_smem ? reinterpret_cast<double*>(smem + 1024) : gws + (size_t)blockIdx.x * per;
+  return {base, base + nx, base + 2 * nx, base + 3 * nx, base + 4 * nx, base + 5 * nx, base + 6 * nx};
+}
+
+// G over a span, in place (kind 0: implicit, 1: explicit).
+__device__ void coarse_block(const Scratch& S, const MacroArgs& a, double* red) {
+  const double dt = a.t_span / a.coarse_steps;
+  for (int s = 0; s < a.coarse_steps; ++s) {
+    if (a.coarse_kind == 0) limit_step_implicit_block(S.w, S.s0, S.s1, S.s2, S.s3, S.s4, S.rs, a, dt, red);
+    else limit_step_block(S.w, S.s0, S.s1, a, dt, red);
+  }
+}
+
+__global__ void coarse_kernel(MacroArgs a, const double* rho_in, double* rho_out, double* gws,
+                              int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = reinterpret_cast<double*>(smem);
+  const int nx = a.nx;
+  Scratch S = scratch_of(smem, gws, nx, in_smem);
+  const double* ri = rho_in + (size_t)blockIdx.x * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = ri[i];
+  __syncthreads();
+  coarse_block(S, a, red);
+  double* ro = rho_out + (size_t)blockIdx.x * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) ro[i] = S.w[i];
+}
+
+template <class G>
+__global__ void lift_kernel(MacroArgs a, const double* rho, G* g, double* gws, int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = reinterpret_cast<double*>(smem);
+  const int nx = a.nx, nv = a.nv;
+  Scratch S = scratch_of(smem, gws, nx, in_smem);
+  const double* ri = rho + (size_t)blockIdx.x * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = ri[i];
+  __syncthreads();
+  poisson_block(S.w, S.s0, nx, a.rho_bar, a.dx, red);
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double r0 = S.w[i], r1 = S.w[i + 1 == nx ? 0 : i + 1];
+    S.s1[i] = (r1 - r0) * a.inv_dx - S.s0[i] * 0.5 * (r0 + r1);
+  }
+  __syncthreads();
+  // g = -eps (xi_j M_j - <xi M> M_j) J_i
+  const double* vM = a.vtab + 2 * nv;  // v_j M_j
+  const double* Mj = a.vtab + 1 * nv;
+  G* gb = g + (size_t)blockIdx.x * nx * nv;
+  const size_t n = (size_t)nx * nv;
+  for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
+    const int i = (int)(q / nv), j = (int)(q % nv);
+    const double J = S.s1[i];
+    gb[q] = (G)(-a.eps * (vM[j] * J - a.xiM * J * Mj[j]));
+  }
+}
+
+// Sequential correction of Algorithm 1 for one solve (one CTA):
+// for n = k..N-1: Gn = G(rho^{n,k+1}); rho^{n+1,k+1} = F + (Gn - Gprev);
+// Gprev = Gn; err = max |rho^{n+1,k+1} - rho^{n+1,k}|.
+__global__ void correct_kernel(CorrectArgs c, double* gws, int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = reinterpret_cast<double*>(smem);
+  const MacroArgs& a = c.m;
+  const int nx = a.nx;
+  Scratch S = scratch_of(smem, gws, nx, in_smem);
+  double emax = 0.0;
+  for (int n = c.k; n < c.n_slices; ++n) {
+    const double* rn = c.rho + (size_t)n * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = rn[i];
+    __syncthreads();
+    coarse_block(S, a, red);
+    double* out = c.rho + (size_t)(n + 1) * nx;
+    const double* F = c.frho + (size_t)(n + 1) * nx;
+    double* Gp = c.gprev + (size_t)(n + 1) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double v = F[i] + (S.w[i] - Gp[i]);
+      emax = fmax(emax, fabs(v - out[i]));
+      out[i] = v;
+      Gp[i] = S.w[i];
+    }
+    __syncthreads();
+  }
+  for (int m = 16; m > 0; m >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, m));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double e = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) e = fmax(e, red[q]);
+    *c.err = e;
+  }
+}
+
+// Coarse guess of Algorithm 1: rho^{n+1,0} = G(rho^{n,0}), Gprev = rho^{n+1,0}.
+__global__ void coarse_chain_kernel(MacroArgs a, int n_slices, double* rho, double* gprev,
+                                    double* gws, int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = reinterpret_cast<double*>(smem);
+  const int nx = a.nx;
+  Scratch S = scratch_of(smem, gws, nx, in_smem);
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = rho[i];
+  __syncthreads();
+  for (int n = 0; n < n_slices; ++n) {
+    coarse_block(S, a, red);
+    double* out = rho + (size_t)(n + 1) * nx;
+    double* Gp = gprev + (size_t)(n + 1) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      out[i] = S.w[i];
+      Gp[i] = S.w[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- launches --
+
+static size_t macro_smem(int nx, bool in_smem) {
+  return 1024 + (in_smem ? 8 * ((size_t)kScratchArrays * nx + kReducedDoubles) : 0);
+}
+static bool macro_fits(int nx) { return macro_smem(nx, true) <= 220 * 1024; }
+
+size_t macro_ws_bytes(int nx, int grid) {
+  return macro_fits(nx) ? 0 : (size_t)grid * ((size_t)kScratchArrays * nx + kReducedDoubles) * sizeof(double);
+}
+
+int coarse_parts(int nx) {
+  int P = 4;
+  while (P < 256 && (long long)(2 * P) * (2 * P) <= nx) P *= 2;
+  if (P > nx / 2) P = nx / 2;
+  return P;
+}
+
+template <class K, class... Args>
+static cudaError_t launch_macro(K kernel, int grid, int nx, double* gws, cudaStream_t s,
+                                Args... args) {
+  const bool in_smem = macro_fits(nx);
+  const size_t smem = macro_smem(nx, in_smem);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e != cudaSuccess) return e;
+  if (!in_smem && gws == nullptr) return cudaErrorInvalidValue;
+  kernel<<<grid, kMacroThreads, smem, s>>>(args..., gws, in_smem ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse(const MacroArgs& a, const double* rho_in, double* rho_out, double* gws,
+                          cudaStream_t s) {
+  return launch_macro(coarse_kernel, a.batch, a.nx, gws, s, a, rho_in, rho_out);
+}
+
+cudaError_t launch_lift(const MacroArgs& a, const double* rho, void* g_out, bool fp32, double* gws,
+                        cudaStream_t s) {
+  if (fp32) return launch_macro(lift_kernel<float>, a.batch, a.nx, gws, s, a, rho, (float*)g_out);
+  return launch_macro(lift_kernel<double>, a.batch, a.nx, gws, s, a, rho, (double*)g_out);
+}
+
+cudaError_t launch_correct(const CorrectArgs& c, double* gws, cudaStream_t s) {
+  return launch_macro(correct_kernel, 1, c.m.nx, gws, s, c);
+}
+
+cudaError_t launch_coarse_chain(const MacroArgs& a, int n_slices, double* rho, double* gprev,
+                                double* gws, cudaStream_t s) {
+  return launch_macro(coarse_chain_kernel, 1, a.nx, gws, s, a, n_slices, rho, gprev);
+}
+
+}  // namespace mmk

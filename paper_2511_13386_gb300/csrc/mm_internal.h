@@ -1,0 +1,101 @@
+// Internal declarations shared by the host API and the kernels of libmm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mm.h"
+
+namespace mmk {
+
+constexpr int kFineThreads = 512;   // threads of one fine CTA (one state)
+constexpr int kVTabFields = 6;      // per velocity node: |v|/dx, M, v M, w v, w, v
+
+// Velocity constants of one context, built on the host in double.
+struct VelocityGrid {
+  int nv = 0;
+  double dv = 0, m2 = 0, xiM = 0;
+  std::vector<double> v, w, M;
+};
+
+// Lane layout of the fine sweep: each interface column is handled by a
+// group of `lanes` consecutive lanes (a power of two <= 32); lane l of the
+// negative half owns nodes [l*vpt, (l+1)*vpt), lane nhp+l of the positive
+// half owns nodes [nv/2 + l*vpt, ...); lanes with l >= nh are idle.
+struct LaneLayout {
+  int vpt = 0, lanes = 0, nh = 0, nhp = 0;
+};
+
+// Arguments of the fine kernel (plain data; device pointers).
+struct FineArgs {
+  int nx, nv, batch;
+  int64_t n_steps;
+  int lanes, nh, nhp;
+  double dt, dx, inv_dx, inv_dv, eps, inv_eps, a, b, m2, dt_dx;
+  double rho_bar;       // NaN: mean of each state's density
+  int adapt, r_scale, flux_rule;
+  double thr_g, thr_R, r_fac;
+  const double* rho_in;
+  double* rho_out;
+  const void* g_in;
+  void* g_buf0;         // step buffers: step s writes buf[(n_steps-1-s)&1]
+  void* g_buf1;         //   so the last step writes buf0 (= g_out)
+  uint8_t* mask_out;
+  const double* vtab;   // [kVTabFields][nv] in double
+  const float* vtab_f;  // same in float
+  void* col_ws;         // per-state column arrays when they do not fit smem
+  size_t col_ws_stride; // bytes per state in col_ws
+  int col_in_smem;      // 1: column arrays in shared memory
+  unsigned long long* kin_count;  // kinetic cell-updates (summed)
+  int* status;          // device status word (mm_status)
+};
+
+// Column-array footprint of one state (bytes), for the chosen precision.
+size_t fine_column_bytes(int nx, int nv, int lanes, bool fp32, bool adapt);
+size_t fine_smem_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool col_in_smem);
+
+// Launch the fine kernel for a batch (one CTA per state).
+cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem,
+                        cudaStream_t s);
+
+// Arguments of the macroscopic kernels (coarse step, lift, correction).
+struct MacroArgs {
+  int nx, nv, batch;
+  double dx, inv_dx, m2, rho_bar, eps, xiM;
+  int coarse_kind, coarse_steps;
+  int parts;            // chunks of the partitioned tridiagonal solve
+  double t_span;
+  const double* vtab;   // [kVTabFields][nv]
+};
+
+// Global scratch (doubles) the macroscopic kernels need for `grid` CTAs when
+// their arrays do not fit shared memory (0 when they fit).
+size_t macro_ws_bytes(int nx, int grid);
+int coarse_parts(int nx);
+cudaError_t launch_coarse(const MacroArgs& a, const double* rho_in, double* rho_out, double* gws,
+                          cudaStream_t s);
+cudaError_t launch_lift(const MacroArgs& a, const double* rho, void* g_out, bool fp32, double* gws,
+                        cudaStream_t s);
+
+// Parareal on the device: the sequential correction sweep over slices
+// n = k..N-1 (one CTA per solve), and the successive-error reduction.
+struct CorrectArgs {
+  MacroArgs m;
+  int n_slices, k;
+  double* rho;          // [N+1][nx]  rho^{n,k} in, rho^{n,k+1} out
+  const double* frho;   // [N+1][nx]  F(rho^{n,k}) at index n+1
+  double* gprev;        // [N+1][nx]  G(rho^{n,k}) at index n+1 (updated)
+  double* err;          // one double: max_n,i |rho^{n,k+1} - rho^{n,k}|
+  double* work;         // [nx] scratch per solve
+};
+cudaError_t launch_correct(const CorrectArgs& a, double* gws, cudaStream_t s);
+cudaError_t launch_coarse_chain(const MacroArgs& a, int n_slices, double* rho, double* gprev,
+                                double* gws, cudaStream_t s);
+
+}  // namespace mmk
+
+// Thread-local error message helpers (mm_api.cpp).
+mm_status mm_fail(mm_status st, const std::string& msg);
+mm_status mm_cuda_fail(cudaError_t e, const char* what);

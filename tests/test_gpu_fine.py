@@ -1,0 +1,194 @@
+"""Parity of the CUDA fine propagator F = S^HMM with the oracle.
+
+FP64 path: <= 1e-12 relative (max-norm) on rho and g, identical masks.
+FP32-g path: <= 1e-5 relative on rho (the FP32 target), mass drift
+<= 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_13386_gb300 import mm, workloads as W
+from tests.gpu_helpers import FP32_TOL, FP64_TOL, oparams, params, rel, run_fine
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [mm.MM_FP64, mm.MM_FP32G]
+
+
+def _check(p, rho, g, span, n_check=None):
+    ro, go, mo, st, q = run_fine(p, rho, g, span)
+    op = oparams(p)
+    B = rho.shape[0]
+    idx = range(B) if n_check is None else np.linspace(0, B - 1, n_check).astype(int)
+    for b in idx:
+        r_ref, g_ref, m_ref, _ = O.fine(op, q["n_steps"], q["dt"], rho[b], g[b])
+        if p.precision == mm.MM_FP64:
+            assert rel(ro[b], r_ref) <= FP64_TOL, (b, rel(ro[b], r_ref))
+            assert rel(go[b], g_ref) <= FP64_TOL * 10, (b, rel(go[b], g_ref))
+            assert np.array_equal(mo[b], m_ref), b
+        else:
+            assert rel(ro[b], r_ref) <= FP32_TOL, (b, rel(ro[b], r_ref))
+            assert rel(go[b], g_ref) <= 1e-3, (b, rel(go[b], g_ref))
+    assert st["device_status"] == 0
+    return ro, go, mo, st, q
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_full_kinetic(prec):
+    """Nx=64, Nv=32, eps=1: one slice of the small workload (8 steps)."""
+    w = W.small()
+    rho, g = w.with_batch(3)
+    p = params(w.nx, w.nv, w.eps, prec, rho_bar=1.0)
+    _, _, mo, st, q = _check(p, rho, g, w.t_end / w.n_slices)
+    assert q["n_steps"] == 8
+    assert st["kinetic_updates"] == 3 * 8 * w.nx * w.nv
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_shape_short_window(prec):
+    """Nx=1024, Nv=64, eps=1e-2 (the batched workload's grid), 40 steps."""
+    w = W.batched()
+    rho, g = w.with_batch(4)
+    p = params(w.nx, w.nv, w.eps, prec, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    _check(p, rho, g, 40 * dt * (1 - 1e-12))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nx,nv", [(8, 4), (13, 12), (100, 20), (777, 48), (2048, 16)])
+def test_ragged_shapes(prec, nx, nv):
+    """Grids that leave ragged tails: odd nx, nx not a multiple of the
+    thread count, nv needing idle lanes (20, 12, 48), the minimum grid."""
+    w = W.batched(nx=nx, nv=nv, eps=0.3)
+    rho, g = w.with_batch(2)
+    p = params(nx, nv, 0.3, prec, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    _check(p, rho, g, 9.5 * dt)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_rho_bar_from_input_mean(prec):
+    w = W.batched(nx=256, nv=32, eps=0.1)
+    rho, g = w.with_batch(2)
+    rho = rho + np.array([[0.01], [-0.02]])
+    p = params(256, 32, 0.1, prec, rho_bar=float("nan"))
+    ro, _, _, _, q = run_fine(p, rho, g, 0.002)
+    for b in range(2):
+        op = oparams(p)
+        op.rho_bar = float(np.mean(rho[b]))
+        r_ref, _, _, _ = O.fine(op, q["n_steps"], q["dt"], rho[b], g[b])
+        assert rel(ro[b], r_ref) <= (FP64_TOL if prec == mm.MM_FP64 else FP32_TOL)
+
+
+def _hybrid(prec, flux_rule=0, nx=512, nv=32):
+    w = W.hybrid(nx=nx, nv=nv, eps=1e-2, v_max=8.0)
+    rho, g = w.with_batch(3)
+    rho = rho + 0.01 * np.cos(2 * np.pi * (np.arange(nx) + 0.5) / nx)[None, :]
+    p = params(nx, nv, 1e-2, prec, rho_bar=1.0, adapt=1, thr_g=1e-3, thr_R=1e-2, r_scale=1,
+               flux_rule=flux_rule)
+    return p, rho, g
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("flux_rule", [0, 1])
+def test_hybrid_adaptation_masks_and_density(prec, flux_rule):
+    """Hybrid S^HMM with both criteria: identical masks (FP64), density
+    parity, and a genuinely mixed kinetic/fluid state."""
+    p, rho, g = _hybrid(prec, flux_rule)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    ro, go, mo, st, q = _check(p, rho, g, 60 * dt)
+    assert 0 < mo.sum() < mo.size
+    assert 0 < st["kinetic_updates"] < st["full_updates"]
+
+
+def test_fp32_mass_conservation_long_window():
+    """FP32-g path over 2000 steps of the batched grid: the density stays
+    within 1e-12 relative mass drift (float-float density and fluxes)."""
+    w = W.batched()
+    rho, g = w.with_batch(2)
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP32G, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    ro, _, _, _, _ = run_fine(p, rho, g, 2000 * dt, mask=False)
+    for b in range(2):
+        assert abs(ro[b].sum() - rho[b].sum()) / rho[b].sum() <= 1e-12
+
+
+def test_host_pointers_match_device_pointers():
+    import torch
+    w = W.small()
+    rho, g = w.with_batch(2)
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP64, rho_bar=1.0)
+    ro_d, go_d, _, _, _ = run_fine(p, rho, g, 0.01)
+    ctx = mm.mm_create(p)
+    ro_h, go_h = np.empty_like(rho), np.empty_like(g)
+    mm.mm_fine_propagate(ctx, 2, 0.01, np.ascontiguousarray(rho), np.ascontiguousarray(g), ro_h,
+                         go_h, stats=True)
+    ctx.close()
+    assert np.array_equal(ro_h, ro_d) and np.array_equal(go_h, go_d)
+
+
+@pytest.mark.parametrize("steps_odd", [True, False])
+def test_in_place_g(steps_odd):
+    import torch
+    w = W.small()
+    rho, g = w.with_batch(2)
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP64, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    span = (7 if steps_odd else 6) * dt * (1 - 1e-9)
+    dev = torch.device("cuda:0")
+    r = torch.tensor(rho, device=dev)
+    gg = torch.tensor(g, device=dev)
+    ro = torch.empty_like(r)
+    mm.mm_fine_propagate(ctx, 2, span, r, gg, ro, gg, stats=True)
+    q = mm.mm_query(ctx, span)
+    ctx.close()
+    r_ref, g_ref, _, _ = O.fine(oparams(p), q["n_steps"], q["dt"], rho[1], g[1])
+    assert rel(gg[1].cpu().numpy(), g_ref) <= 1e-11
+    assert rel(ro[1].cpu().numpy(), r_ref) <= FP64_TOL
+
+
+def test_invalid_arguments_are_rejected():
+    import torch
+    p = params(64, 32, 1.0, mm.MM_FP64)
+    ctx = mm.mm_create(p)
+    x = torch.zeros((1, 64), dtype=torch.float64, device="cuda:0")
+    g = torch.zeros((1, 64, 32), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_fine_propagate(ctx, 1, -1.0, x, g, x, g)
+    assert e.value.status == mm.MM_ERR_INVALID
+    with pytest.raises(mm.MMError):
+        mm.mm_fine_propagate(ctx, -2, 0.1, x, g, x, g)
+    assert mm.mm_fine_propagate(ctx, 0, 0.1, x, g, x, g, stats=True)["steps"] == 0
+    ctx.close()
+    with pytest.raises(mm.MMError):
+        mm.mm_create(params(64, 34, 1.0, mm.MM_FP64))   # 34/2 = 17: no lane layout
+    with pytest.raises(mm.MMError):
+        mm.mm_create(params(4, 32, 1.0, mm.MM_FP64))
+    bad = params(64, 32, 1.0, mm.MM_FP64, dt=1.0)
+    c2 = mm.mm_create(bad)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_fine_propagate(c2, 1, 0.1, x, g, x, g)
+    assert e.value.status == mm.MM_ERR_UNSTABLE
+    c2.close()
+
+
+@pytest.mark.parametrize("w", [W.small(), W.batched(), W.hybrid()], ids=["small", "batched", "hybrid"])
+def test_step_rule_matches_oracle(w):
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP64, v_max=w.v_max, adapt=int(w.adapt))
+    ctx = mm.mm_create(p)
+    span = w.t_end / w.n_slices
+    q = mm.mm_query(ctx, span)
+    ctx.close()
+    lim = O.dt_limit(oparams(p))
+    assert q["n_steps"] == int(np.ceil(span / lim))
+    assert q["dt_limit"] == pytest.approx(lim, rel=1e-12)

@@ -1,0 +1,47 @@
+"""Parity at full size, in the launch configuration the benchmark times:
+the batched workload (Nx=1024, Nv=64, eps=1e-2) with all 128 slice states
+propagated over one full slice (T/N = 1/128, 7112 steps) in one launch.
+The oracle recomputes two sampled states; every state is checked for mass
+conservation and finiteness."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_13386_gb300 import mm, workloads as W
+from tests.gpu_helpers import FP32_TOL, FP64_TOL, device, gdtype, oparams, params, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N_STATES = 128
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP32G, mm.MM_FP64])
+def test_full_slice_all_states_sampled(prec):
+    dev = device()
+    w = W.batched()
+    rho_b, g_b = w.with_batch(8)
+    rho = np.tile(rho_b, (N_STATES // 8, 1))
+    g = np.tile(g_b, (N_STATES // 8, 1, 1))
+    p = params(w.nx, w.nv, w.eps, prec, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    span = w.t_end / w.n_slices
+    q = mm.mm_query(ctx, span)
+    assert q["n_steps"] == 7112
+    r = torch.tensor(rho, device=dev)
+    gg = torch.tensor(g, device=dev, dtype=gdtype(prec))
+    ro, go = torch.empty_like(r), torch.empty_like(gg)
+    st = mm.mm_fine_propagate(ctx, N_STATES, span, r, gg, ro, go, stats=True)
+    ctx.close()
+    assert st["device_status"] == 0
+    assert st["kinetic_updates"] == N_STATES * 7112 * w.nx * w.nv
+    ro = ro.cpu().numpy()
+    assert np.isfinite(ro).all()
+    mass_in, mass_out = rho.sum(axis=1), ro.sum(axis=1)
+    assert np.abs(mass_out - mass_in).max() / mass_in.max() <= 1e-12
+    op = oparams(p)
+    for b in (3, 101):
+        r_ref, g_ref, _, _ = O.fine(op, q["n_steps"], q["dt"], rho[b], g[b])
+        tol = FP64_TOL if prec == mm.MM_FP64 else FP32_TOL
+        assert rel(ro[b], r_ref) <= tol, (b, rel(ro[b], r_ref))
+        assert rel(go[b].double().cpu().numpy(), g_ref) <= (1e-10 if prec == mm.MM_FP64 else 1e-3)

@@ -1,0 +1,115 @@
+"""Parity of the coarse propagator, the lifting and the device parareal loop
+(Algorithm 1) with the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_13386_gb300 import mm, workloads as W
+from tests.gpu_helpers import (FP32_TOL, FP64_TOL, device, gdtype, oparams, params,
+                               parareal_with_sensitivity, rel)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind,steps", [(0, 1), (0, 3), (1, 1)])
+@pytest.mark.parametrize("nx", [64, 1024, 4096])
+def test_coarse_parity(kind, steps, nx):
+    dev = device()
+    w = W.batched(nx=nx, nv=16, eps=1e-2)
+    rho, _ = w.with_batch(3)
+    p = params(nx, 16, 1e-2, mm.MM_FP64, rho_bar=1.0, coarse_kind=kind, coarse_steps=steps)
+    ctx = mm.mm_create(p)
+    span = 1.0 / 128
+    r = torch.tensor(rho, device=dev)
+    out = torch.empty_like(r)
+    mm.mm_coarse(ctx, 3, span, r, out)
+    out = out.cpu().numpy()
+    ctx.close()
+    op = oparams(p)
+    n_sub = steps
+    if kind == 1:
+        _, _, _, m2 = O.velocity_grid(op)
+        lim = 0.9 * (1.0 / nx) ** 2 / (2 * m2)
+        n_sub = max(steps, int(np.ceil(span / lim)))
+    for b in range(3):
+        ref = O.coarse(op, span, rho[b], kind=kind, n_sub=n_sub)
+        assert rel(out[b], ref) <= FP64_TOL, rel(out[b], ref)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32G])
+def test_lift_parity(prec):
+    dev = device()
+    w = W.batched(nx=512, nv=64, eps=1e-2)
+    rho, _ = w.with_batch(2)
+    p = params(512, 64, 1e-2, prec, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    r = torch.tensor(rho, device=dev)
+    g = torch.empty((2, 512, 64), device=dev, dtype=gdtype(prec))
+    mm.mm_lift(ctx, 2, r, g)
+    ctx.close()
+    for b in range(2):
+        ref = O.lift(oparams(p), rho[b])
+        tol = FP64_TOL if prec == mm.MM_FP64 else 1e-6
+        assert rel(g[b].double().cpu().numpy(), ref) <= tol
+
+
+def _parareal(prec, w, K, tol=0.0, **kw):
+    dev = device()
+    p = params(w.nx, w.nv, w.eps, prec, v_max=w.v_max, rho_bar=1.0, **kw)
+    ctx = mm.mm_create(p)
+    out = torch.empty((w.n_slices + 1, w.nx), dtype=torch.float64, device=dev)
+    info = mm.parareal_run(ctx, w.t_end, w.n_slices, K, tol, torch.tensor(w.rho0, device=dev),
+                           torch.tensor(w.g0, device=dev, dtype=gdtype(prec)), out)
+    ctx.close()
+    return p, out.cpu().numpy(), info
+
+
+def test_parareal_small_workload():
+    """The small workload (FP64): Nx=64, Nv=32, eps=1, T=0.05, N=4, K=4.
+    Slices 0 and 1 (one fine propagation from the given data) at 1e-12;
+    the later slices within the oracle's own rounding sensitivity."""
+    w = W.small()
+    p, out, info = _parareal(mm.MM_FP64, w, w.max_iter)
+    ref, err, it, sens = parareal_with_sensitivity(oparams(p), w, w.max_iter)
+    assert info["iterations"] == it
+    assert rel(out[:2], ref[:2]) <= FP64_TOL
+    assert rel(out, ref) <= max(FP64_TOL, 20 * sens), (rel(out, ref), sens)
+    assert np.allclose(info["err"], err, rtol=1e-6, atol=1e-14)
+    assert info["mass_drift"] <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32G])
+def test_parareal_batched_grid_reduced_span(prec):
+    """The batched workload's grid (Nx=1024, Nv=64, eps=1e-2) with N=6
+    slices over a short span, K=3, and stopping on a tolerance."""
+    w = W.batched(n_slices=6)
+    w.t_end = 6 * 25 * 1.0986e-6
+    p, out, info = _parareal(prec, w, 3)
+    ref, err, it = O.parareal(oparams(p), w.rho0, w.g0, w.t_end, w.n_slices, 3)
+    assert info["iterations"] == it
+    tol = FP64_TOL if prec == mm.MM_FP64 else FP32_TOL
+    assert rel(out, ref) <= tol, rel(out, ref)
+    # tolerance stop: same iteration count as the oracle
+    p2, out2, info2 = _parareal(prec, w, 6, tol=err[1] * 1.0001)
+    ref2, err2, it2 = O.parareal(oparams(p2), w.rho0, w.g0, w.t_end, w.n_slices, 6, tol=err[1] * 1.0001)
+    assert info2["iterations"] == it2 == 2
+
+
+def test_parareal_reproduces_sequential_at_K_equals_N():
+    w = W.small(nx=64, nv=32)
+    p, out, info = _parareal(mm.MM_FP64, w, w.n_slices)
+    seq = O.sequential(oparams(p), w.rho0, w.g0, w.t_end, w.n_slices)
+    _, _, _, sens = parareal_with_sensitivity(oparams(p), w, w.n_slices)
+    assert rel(out, seq) <= max(FP64_TOL, 20 * sens), (rel(out, seq), sens)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32G])
+def test_parareal_hybrid(prec):
+    """Parareal with domain adaptation on (hybrid bump, small grid)."""
+    w = W.hybrid(nx=256, nv=32, eps=1e-2, n_slices=4, v_max=8.0)
+    w.t_end = 4 * 30 * 4.0e-6
+    p, out, info = _parareal(prec, w, 2, adapt=1, thr_g=1e-3, thr_R=1e-2, r_scale=1)
+    ref, err, it = O.parareal(oparams(p), w.rho0, w.g0, w.t_end, w.n_slices, 2)
+    tol = FP64_TOL if prec == mm.MM_FP64 else FP32_TOL
+    assert rel(out, ref) <= tol, rel(out, ref)
