@@ -182,6 +182,39 @@ MM_API mm_status mm_fine_propagate(mm_ctx* ctx, int32_t batch, double t_span,
                             double* rho_out, void* g_out, uint8_t* mask_out,
                             mm_fine_stats* stats, void* stream);
 
+/* Size in bytes of the fixed device scratch array of
+   mm_fine_propagate_noalloc (64 MiB, held by every GPU that loads the
+   library until the process exits). */
+#define MM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* mm_fine_propagate for callers that cannot allocate device memory when
+   they run F.  The paper has no counterpart: this is a deployment variant of
+   the same kernel.  Such callers -- an application whose memory is all
+   handed to its own pool, a real-time loop that must not reach the
+   allocator or risk an out-of-memory failure mid-run -- create the context
+   once at start-up (mm_create allocates its small velocity tables there)
+   and then call this entry point, which allocates nothing: the scratch of
+   the fine kernel (second step buffer of g, status word, the column arrays
+   when they do not fit shared memory, and a copy of g_in when it aliases
+   g_out with an odd step count) lives in a static device array of
+   MM_NOALLOC_SCRATCH_BYTES inside the library.
+   Arguments and results are those of mm_fine_propagate, with three
+   differences: every array must be a 16-byte aligned device pointer (host
+   arrays would need staging buffers); stats->elapsed_ms is 0; the call's
+   scratch must fit the array.
+   The first call on a device looks up the array's device address on that
+   device (cudaGetSymbolAddress), so make that first call before any stream
+   capture.  Every call shares the one array and the array keeps the last
+   call's contents: calls that may run at the same time on the GPU (on
+   streams with no ordering between them) race on it and must not be issued.
+   Errors: MM_ERR_INVALID (as mm_fine_propagate; host or unaligned array;
+   scratch needed above MM_NOALLOC_SCRATCH_BYTES, with the size in the
+   message), MM_ERR_UNSTABLE, MM_ERR_CUDA. */
+MM_API mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, double t_span,
+                                    const double* rho_in, const void* g_in,
+                                    double* rho_out, void* g_out, uint8_t* mask_out,
+                                    mm_fine_stats* stats, void* stream);
+
 /* G over a span (Sec. 2.3, eq. S^0): coarse_steps linearly implicit steps
    (E frozen from the old density, cyclic tridiagonal solve) or explicit S^0
    steps, for every density of the batch.  rho_in and rho_out may alias.

@@ -700,3 +700,61 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   cudaEventDestroy(e1);
   return MM_OK;
 }
+
+// --------------------------------------------- fine plan without buffers --
+
+// Kernel arguments of F for one call, with every buffer pointer left unset
+// (used by the entry point that takes its scratch from static device
+// memory instead of the workspace).
+mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (batch < 0) return mm_fail(MM_ERR_INVALID, "batch must be >= 0");
+  if (!(t_span > 0)) return mm_fail(MM_ERR_INVALID, "t_span must be > 0");
+  if (c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
+    return mm_fail(MM_ERR_UNSTABLE, "params.dt is above the stability limit");
+  const mm_params& p = c->p;
+  const int64_t n = steps_for(t_span, c->dt_limit);
+  const double dt = t_span / n;
+  FinePlan f{};
+  f.device = c->device;
+  f.fp32 = p.precision == MM_FP32G;
+  f.vpt = c->lay.vpt;
+  f.n_steps = n;
+  f.g_bytes = (size_t)batch * p.nx * p.nv * (f.fp32 ? 4 : 8);
+  f.rho_bytes = (size_t)batch * p.nx * 8;
+  const bool adapt = p.adapt != 0;
+  f.col_in_smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, true) <= 232448;
+  f.col_bytes = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt);
+  f.smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, f.col_in_smem);
+  FineArgs& a = f.args;
+  a.nx = p.nx;
+  a.nv = p.nv;
+  a.batch = batch;
+  a.n_steps = n;
+  a.lanes = c->lay.lanes;
+  a.nh = c->lay.nh;
+  a.nhp = c->lay.nhp;
+  a.dt = dt;
+  a.dx = p.x_len / p.nx;
+  a.inv_dx = 1.0 / a.dx;
+  a.inv_dv = 1.0 / c->vg.dv;
+  a.eps = p.eps;
+  a.inv_eps = 1.0 / p.eps;
+  a.a = exp(-dt / (p.eps * p.eps));
+  a.b = p.eps * (1.0 - a.a);
+  a.m2 = c->vg.m2;
+  a.dt_dx = dt / a.dx;
+  a.rho_bar = p.rho_bar;
+  a.adapt = p.adapt;
+  a.r_scale = p.r_scale;
+  a.flux_rule = p.flux_rule;
+  a.thr_g = p.thr_g;
+  a.thr_R = p.thr_R;
+  a.r_fac = p.r_scale ? p.eps * p.eps : 1.0;
+  a.vtab = c->d_vtab;
+  a.vtab_f = c->d_vtab_f;
+  a.col_in_smem = f.col_in_smem ? 1 : 0;
+  a.col_ws_stride = f.col_in_smem ? 0 : f.col_bytes;
+  *out = f;
+  return MM_OK;
+}

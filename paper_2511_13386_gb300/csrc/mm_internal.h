@@ -94,6 +94,17 @@ cudaError_t launch_correct(const CorrectArgs& a, double* gws, cudaStream_t s);
 cudaError_t launch_coarse_chain(const MacroArgs& a, int n_slices, double* rho, double* gprev,
                                 double* gws, cudaStream_t s);
 
+// Everything the fine kernel needs for one call except its buffers: the
+// arguments (pointers unset), the template choice and the byte counts.
+struct FinePlan {
+  FineArgs args;
+  int device, vpt;
+  bool fp32, col_in_smem;
+  int64_t n_steps;
+  size_t g_bytes, rho_bytes, col_bytes, smem;
+};
+mm_status fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out);
+
 }  // namespace mmk
 
 // Thread-local error message helpers (mm_api.cpp).

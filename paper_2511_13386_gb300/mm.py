@@ -27,7 +27,7 @@ STATUS_NAMES = ["MM_OK", "MM_ERR_INVALID", "MM_ERR_OOM", "MM_ERR_CUDA", "MM_ERR_
                 "MM_ERR_UNSTABLE", "MM_ERR_BUSY", "MM_ERR_NOT_READY", "MM_ERR_UNKNOWN_TICKET"]
 
 EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine_propagate",
-            "mm_coarse", "mm_lift", "parareal_run", "mm_server_create", "serve_submit",
+            "mm_fine_propagate_noalloc", "mm_coarse", "mm_lift", "parareal_run", "mm_server_create", "serve_submit",
             "serve_poll", "mm_server_destroy", "mm_last_error"]
 
 
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True):
             "mm_query": (ctypes.c_int, [V, ctypes.c_double, P(mm_info)]),
             "mm_fine_propagate": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V, V, V,
                                                  P(mm_fine_stats), V]),
+            "mm_fine_propagate_noalloc": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V,
+                                                         V, V, P(mm_fine_stats), V]),
             "mm_coarse": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V]),
             "mm_lift": (ctypes.c_int, [V, ctypes.c_int32, V, V, V]),
             "parareal_run": (ctypes.c_int, [V, P(mm_parareal_cfg), V, V, V, P(mm_parareal_stats), V]),
@@ -210,6 +212,21 @@ def mm_fine_propagate(ctx: Ctx, batch: int, t_span: float, rho_in, g_in, rho_out
                                     ctypes.byref(st) if st is not None else None,
                                     _stream(stream)))
     return {f: getattr(st, f) for f, _ in mm_fine_stats._fields_} if st is not None else None
+
+
+def mm_fine_propagate_noalloc(ctx: Ctx, batch: int, t_span: float, rho_in, g_in, rho_out, g_out,
+                              mask_out=None, stats: bool = False, stream=None):
+    """F with the library's fixed device scratch instead of allocated
+    workspace (device arrays only; see include/mm.h)."""
+    st = mm_fine_stats() if stats else None
+    _check(load().mm_fine_propagate_noalloc(ctx.handle, batch, t_span, _ptr(rho_in), _ptr(g_in),
+                                            _ptr(rho_out), _ptr(g_out), _ptr(mask_out),
+                                            ctypes.byref(st) if st is not None else None,
+                                            _stream(stream)))
+    return {f: getattr(st, f) for f, _ in mm_fine_stats._fields_} if st is not None else None
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def mm_coarse(ctx: Ctx, batch: int, t_span: float, rho_in, rho_out, stream=None):
