@@ -116,6 +116,15 @@ typedef struct {
                           max(coarse_steps, the steps its stability needs) */
   int32_t lift_order;  /* lifting order L of Def. 1; 1 is implemented */
   int32_t precision;   /* mm_precision */
+  int32_t fine_kernel; /* F implementation: 0 = automatic; 1 = streaming
+                          (one CTA per state, g in device memory, every
+                          option); 2 = resident (g held in the shared memory
+                          of a thread-block cluster for the whole call; FP32
+                          g, adapt == 0, flux_rule == 0, nv = 8 * {2..32},
+                          nx / cluster size a multiple of 32 and <= 256,
+                          and a multiple of 4 * 256 / (nv / 8);
+                          MM_ERR_INVALID otherwise).  Automatic picks the
+                          resident kernel whenever it applies. */
 } mm_params;
 
 typedef struct mm_ctx mm_ctx;
@@ -142,7 +151,8 @@ typedef struct {
 
 /* Fill *p with defaults: x_len 1, v_max 8, eps 1, rho_bar NaN, adapt 0,
    thr_g 1e-3, thr_R 1e-2, r_scale 0, flux_rule 0, dt 0, cfl_theta 0.9,
-   coarse_kind 0, coarse_steps 1, lift_order 1, precision MM_FP64. */
+   coarse_kind 0, coarse_steps 1, lift_order 1, precision MM_FP64,
+   fine_kernel 0. */
 MM_API void mm_params_default(mm_params* p);
 
 /* Create a context for one problem shape.  Validates the parameters,

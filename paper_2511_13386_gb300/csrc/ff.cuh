@@ -85,6 +85,9 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 __device__ __forceinline__ ff ff_shfl_up(ff a, int d) {
   return {__shfl_up_sync(0xffffffffu, a.hi, d), __shfl_up_sync(0xffffffffu, a.lo, d)};
 }
+__device__ __forceinline__ ff ff_shfl_down(ff a, int d) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, d), __shfl_down_sync(0xffffffffu, a.lo, d)};
+}
 __device__ __forceinline__ ff ff_shfl_xor(ff a, int m) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
 }

@@ -213,6 +213,12 @@ static mm_status validate(const mm_params* p) {
   if (p->dt < 0 || !(p->cfl_theta >= 0)) return mm_fail(MM_ERR_INVALID, "dt and cfl_theta must be >= 0");
   if (p->adapt && (!(p->thr_g >= 0) || !(p->thr_R >= 0)))
     return mm_fail(MM_ERR_INVALID, "thresholds must be >= 0");
+  if (p->fine_kernel < 0 || p->fine_kernel > 2) return mm_fail(MM_ERR_INVALID, "fine_kernel must be 0, 1 or 2");
+  if (p->fine_kernel == 2) {
+    size_t sm;
+    if (!mmk::fine_resident_cluster(p->nx, p->nv, p->precision == MM_FP32G, p->adapt != 0, p->flux_rule, &sm))
+      return mm_fail(MM_ERR_INVALID, "fine_kernel 2 (resident) does not support this shape or option set");
+  }
   return MM_OK;
 }
 
@@ -346,11 +352,15 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   if (mask_out && (st = device_view(c, WS_MASK, mask_out, mbytes, false, s, &d_mask, &s_mask)) != MM_OK)
     return st;
 
-  void* buf1;
-  if ((st = c->ws.get(WS_GBUF1, gbytes, s, &buf1)) != MM_OK) return st;
+  const bool adapt = p.adapt != 0;
+  size_t res_smem = 0;
+  const int res_C = p.fine_kernel == 1 ? 0 : mmk::fine_resident_cluster(p.nx, p.nv, fp32, adapt, p.flux_rule, &res_smem);
+
+  void* buf1 = nullptr;
+  if (!res_C && (st = c->ws.get(WS_GBUF1, gbytes, s, &buf1)) != MM_OK) return st;
   // g_out is the buffer the last step writes; with an odd step count the
   // first step writes it too, so an aliased input is moved aside first.
-  if (d_gin == d_gout && (n & 1)) {
+  if (!res_C && d_gin == d_gout && (n & 1)) {
     CK(cudaMemcpyAsync(buf1, d_gin, gbytes, cudaMemcpyDeviceToDevice, s), "alias copy");
     d_gin = buf1;
     void* other;
@@ -392,11 +402,10 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.vtab = c->d_vtab;
   a.vtab_f = c->d_vtab_f;
 
-  const bool adapt = p.adapt != 0;
   const size_t colb = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt);
   const bool in_smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, true) <= 232448;
   a.col_in_smem = in_smem ? 1 : 0;
-  if (!in_smem) {
+  if (!in_smem && !res_C) {
     if ((st = c->ws.get(WS_COLS, colb * batch, s, &a.col_ws)) != MM_OK) return st;
     a.col_ws_stride = colb;
   }
@@ -413,7 +422,8 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
     cudaEventRecord(e0, s);
   }
   const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, in_smem);
-  cudaError_t e = mmk::launch_fine(a, c->lay.vpt, fp32, smem, s);
+  cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s)
+                        : mmk::launch_fine(a, c->lay.vpt, fp32, smem, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
   if (stats) cudaEventRecord(e1, s);
 

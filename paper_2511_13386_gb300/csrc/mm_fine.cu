@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
   // moments m+- of the current g from the lane partials (own cells)
   auto moments = [&](int c) {
     G sp = 0, sm = 0;
-    const G* pp = C.part + (size_t)c * Lg;
+    const G* pp = C.part + c * Lg;
     for (int l = 0; l < Lg; ++l) {
       if (l >= A.nhp) sp += pp[l];
       else sm += pp[l];
@@ -416,11 +416,13 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
     // Poisson law: S_c = sum_{m<=c} (rho_m - rho_bar) dx ; E = S - mean(S),
     // with mean(S) = sum_m (nx - m) d_m / nx.
     R t1 = M::zero(), t2 = M::zero();
+    G wgt = G(nx - c0);  // nx - c, counted down without an int conversion
     for (int c = c0; c < c1; ++c) {
       const R d = M::mul(M::sub(C.rho[c], Rrb), Rdx);
       t1 = M::add(t1, d);
       C.S[c] = t1;
-      t2 = M::add(t2, M::mulg(d, (G)(nx - c)));
+      t2 = M::add(t2, M::mulg(d, wgt));
+      wgt -= G(1);
     }
     R inc = t1;
 #pragma unroll
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
     G* eg = C.par;  // E^n goes through the par array's first slot first
     for (int c = c0; c < c1; ++c) {
       const R E = M::sub(M::add(base, C.S[c]), meanS);
-      eg[4 * (size_t)c + 3] = (G)M::tog(E);          // temporary: E in slot 3
+      eg[4 * c + 3] = (G)M::tog(E);          // temporary: E in slot 3
       if constexpr (ADAPT) { C.ed[c] = M::tod(E); C.rd[c] = M::tod(C.rho[c]); }
     }
     __syncthreads();  // rho final for this step; E of all cells visible
@@ -497,8 +499,8 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
                           d1r * (C.jd[c] - meanJ);
         const bool big_R = A.r_fac * fabs(Rc) > A.thr_R;
         double nl = 0.0, nr = 0.0;
-        const G* pl = C.n2 + (size_t)wrapi(c - 1, nx) * Lg;
-        const G* pr = C.n2 + (size_t)c * Lg;
+        const G* pl = C.n2 + wrapi(c - 1, nx) * Lg;
+        const G* pr = C.n2 + c * Lg;
         for (int q = 0; q < Lg; ++q) { nl += (double)pl[q]; nr += (double)pr[q]; }
         nl = sqrt(nl); nr = sqrt(nr);
         uint8_t s;
@@ -537,13 +539,13 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
     // J and the sweep constants: E+/dv, E-/dv, P = <X>, J
     for (int c = c0; c < c1; ++c) {
       const int cl = wrapi(c - 1, nx), cr = wrapi(c + 1, nx);
-      G* pr = C.par + 4 * (size_t)c;
+      G* pr = C.par + 4 * c;
       const G e = pr[3];
       const G J = M::flux_J(C.rho[c], C.rho[cr], e, g_inv_dx);
       C.jg[c] = J;
       const G ep = e > G(0) ? e : G(0), em = e < G(0) ? -e : G(0);
       const G pm = ((C.mp[c] - C.mp[cl]) - (C.mm[cr] - C.mm[c])) * g_inv_dx;
-      const G* en = C.ends + 4 * (size_t)c;
+      const G* en = C.ends + 4 * c;
       const G gend = (G)0.5 * ((ep * en[2] - em * en[3]) - (ep * en[0] - em * en[1]));
       pr[0] = ep * g_inv_dv;
       pr[1] = em * g_inv_dv;
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
   // rule of S^HMM when flux_rule == 1.
   auto flux_kin = [&](int c) {
     Acc s = M::azero();
-    const G* pp = C.part + (size_t)c * Lg;
+    const G* pp = C.part + c * Lg;
     for (int q = 0; q < Lg; ++q) s = M::aadd(s, pp[q]);
     return (G)M::aval(s, g_kflux);
   };
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
 #pragma unroll
     for (int k = 0; k < VPT; ++k) R0[k] = R1[k] = R2[k] = R3[k] = G(0);
     int last = -10;
-    auto col = [&](int i) { return src + (size_t)wrapi(i, nx) * nv + j0; };
+    auto col = [&](int i) { return src + (unsigned)(wrapi(i, nx) * nv + j0); };
     // one interface column: P = g(i-1), Cc = g(i), N = g(i+1), F = g(i+2)
     // (in flight); afterwards P receives g(i+3).
     auto body = [&](int e, G(&P)[VPT], G(&Cc)[VPT], G(&N)[VPT], G(&F)[VPT]) {
@@ -623,13 +625,13 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
         G out[VPT];
         G psum = 0, nsum = 0;
         if (kin) {
-          const float4* pr4 = reinterpret_cast<const float4*>(C.par + 4 * (size_t)i);
+          const float4* pr4 = reinterpret_cast<const float4*>(C.par + 4 * i);
           G Ep, Em, Pp, Jv;
           if constexpr (sizeof(G) == 4) {
             const float4 q = *pr4;
             Ep = q.x; Em = q.y; Pp = q.z; Jv = q.w;
           } else {
-            const G* pr = C.par + 4 * (size_t)i;
+            const G* pr = C.par + 4 * i;
             Ep = pr[0]; Em = pr[1]; Pp = pr[2]; Jv = pr[3];
           }
           G Gl = first_lane ? G(0) : (Ep * left_nb - Em * Cc[0]);
@@ -654,11 +656,11 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
           for (int k = 0; k < VPT; ++k) out[k] = G(0);
         }
         if (active) {
-          vstore<G, VPT>(dst + (size_t)i * nv + j0, out);
+          vstore<G, VPT>(dst + (unsigned)(i * nv + j0), out);
           if (valid) vload<G, VPT>(P, col(i + 3));
         }
-        C.part[(size_t)i * Lg + lig] = psum;
-        if constexpr (ADAPT) C.n2[(size_t)i * Lg + lig] = nsum;
+        C.part[i * Lg + lig] = psum;
+        if constexpr (ADAPT) C.n2[i * Lg + lig] = nsum;
         if constexpr (VPT >= 2) {
           if (first_lane) { C.ends[4 * i + 0] = out[0]; C.ends[4 * i + 1] = out[1]; }
           if (last_lane) { C.ends[4 * i + 2] = out[VPT - 2]; C.ends[4 * i + 3] = out[VPT - 1]; }
@@ -727,7 +729,9 @@ static cudaError_t launch_v(const FineArgs& a, size_t smem, cudaStream_t s) {
   return a.col_in_smem ? launch_t<G, VPT, false, true>(a, smem, s) : launch_t<G, VPT, false, false>(a, smem, s);
 }
 
-cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem, cudaStream_t s) {
+cudaError_t launch_fine(const FineArgs& args, int vpt, bool fp32, size_t smem, cudaStream_t s) {
+  FineArgs a = args;
+  fine_args_floats(a);
   if (fp32) {
     switch (vpt) {
       case 1: return launch_v<float, 1>(a, smem, s);

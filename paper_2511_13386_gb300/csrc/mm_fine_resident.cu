@@ -1,0 +1,551 @@
+// Fine propagator F = S^MM (Sec. 2.3) with the slice states resident in
+// shared memory: FP32 g, every cell kinetic, one flux per interface.
+//
+// A state (rho[nx], g[nx][nv]) is split over a thread-block cluster of C
+// CTAs (C = 1, 2, 4 or 8, the smallest that fits the state into the
+// cluster's shared memory); CTA r owns the cells and interfaces
+// [r nx/C, (r+1) nx/C).  g never leaves shared memory between the first
+// and the last step of the launch, so HBM and L2 see only the initial load
+// and the final store; each step is bound by shared-memory and FP32 issue.
+//
+// Per step n -> n+1:
+//   sweep      every group of `LG` lanes updates a run of interface columns
+//              in place (upwind v d_x g, E d_v g, (I - Pi), relaxation),
+//              from a register ring holding the old columns i-1, i, i+1 and
+//              a prefetch; the old columns it needs from the neighbouring
+//              groups are read (the left one) or copied to a stash (the
+//              right one) before the barrier that precedes the sweep; the
+//              per-lane partial moments <w v g> of the new column are stored;
+//   macro (i)  per cell: the interface flux F = (dt/dx) <xi g>/eps by a
+//              compensated sum of the partials, m+- = <v^+- g>, the warp
+//              sums of F, and the boundary values the neighbouring warps and
+//              CTAs need; the CTA's first and last new columns are copied
+//              into the neighbouring CTAs' halo buffers;
+//   exchange   one barrier per step (cluster-wide when C > 1); every
+//              exchange buffer is double-buffered by step parity, so one
+//              barrier separates each write from its read and the next write;
+//   macro (ii) per cell: rho^{n+1} = rho^n + F_{i-1/2} - F_{i+1/2}; the
+//              field by the discrete Ampere identity (below); J, P = <X> and
+//              the sweep constants of the next step.
+//
+// The Poisson law of S^MM, E_{i+1/2} - E_{i-1/2} = (rho_i - rho_bar) dx with
+// a mean-zero gauge, is solved once at entry (prefix sum in double).  After
+// that, summing the density update over cells m <= i telescopes the fluxes,
+// so the same law at n+1 is exactly
+//   E^{n+1}_{i+1/2} = E^n_{i+1/2} - dx (F_{i+1/2} - mean_k F_{k+1/2}),
+// which needs one global sum per step instead of a prefix sum (it relies on
+// the one-flux-per-interface density update, so the cell-based rule keeps
+// the streaming kernel).
+//
+// Precision: g, the sweep and the per-lane partials in float; the density
+// and the field in float-float; the flux by compensated summation.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "ff.cuh"
+#include "mm_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace mmk {
+
+namespace {
+
+constexpr int T = kResThreads;
+constexpr int NW = T / 32;
+constexpr int VPT = 8;  // velocity nodes per lane (two 16-byte chunks)
+
+// Shared-memory map (byte offsets).  g columns are stored with the lane's
+// two 16-byte chunks interleaved across the group (chunk q of lane l at
+// (q * LG + l) * 16), so that eight consecutive lanes touch 128 contiguous
+// bytes per access and no bank is hit twice.
+struct ResMap {
+  unsigned g, halo, stash, part, par, wfirst, wlast, xch, pro, red, total;
+  unsigned xch_stride;  // bytes per parity in xch
+};
+
+__host__ __device__ inline unsigned up16(unsigned x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline ResMap res_map(int n, int nv, int lanes, int C) {
+  ResMap m;
+  unsigned o = 0;
+  m.g = o;      o = up16(o + 4u * n * nv);
+  m.halo = o;   o = up16(o + 4u * 4 * nv);          // [parity][left, right][nv]
+  m.part = o;   o = up16(o + 4u * n * lanes);
+  m.stash = o;  o = up16(o + 4u * (T / lanes) * nv);  // per group: next group's old first column
+  m.par = o;    o = up16(o + 16u * n);
+  m.wfirst = o; o = up16(o + 16u * NW);             // per warp: F, m-, rho.hi, rho.lo
+  m.wlast = o;  o = up16(o + 16u * NW);             // per warp: F, m+
+  m.xch_stride = up16(16u + 4u * C * NW);           // xL(F, m+), xR(F, m-), sums
+  m.xch = o;    o = up16(o + 2u * m.xch_stride);
+  m.pro = o;    o = up16(o + 32u * C);              // entry exchange, per rank
+  m.red = o;    o = up16(o + 16u * NW);
+  m.total = o;
+  return m;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// Remote (DSMEM) view of this CTA's shared address `p` in cluster rank r.
+template <class P>
+__device__ __forceinline__ P* remote(P* p, int r) {
+  return cg::this_cluster().map_shared_rank(p, r);
+}
+
+__device__ __forceinline__ void cluster_or_block_sync(int C) {
+  if (C > 1) cg::this_cluster().sync();
+  else __syncthreads();
+}
+
+// Block-wide inclusive scan (double) of one value per thread; returns the
+// inclusive prefix and writes the block total to *tot.  red: NW doubles.
+__device__ double block_scan_d(double v, double* red, double* tot) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int d = 1; d < 32; d <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, d);
+    if (l >= d) v += t;
+  }
+  __syncthreads();
+  if (l == 31) red[w] = v;
+  __syncthreads();
+  double off = 0.0, all = 0.0;
+  for (int q = 0; q < NW; ++q) {
+    if (q < w) off += red[q];
+    all += red[q];
+  }
+  __syncthreads();
+  *tot = all;
+  return off + v;
+}
+
+template <int LG>
+__global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, int C) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int HALF = LG / 2;
+  constexpr int NGRP = T / LG;
+
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nx = A.nx, nv = A.nv;
+  const int n = nx / C;                  // cells (and interfaces) of this CTA
+  const int r = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int st = blockIdx.x / C;         // state
+  const int a = r * n;                   // first global cell of this CTA
+  const int rl = (r + C - 1) % C, rr = (r + 1) % C;
+  const int nwc = n >> 5;                // warps that own cells
+  const bool has_cell = tid < n;
+  const int R = n / NGRP;                // columns per group
+
+  const ResMap Mp = res_map(n, nv, LG, C);
+  float* g = reinterpret_cast<float*>(smem + Mp.g);
+  float* halo = reinterpret_cast<float*>(smem + Mp.halo);
+  float* part = reinterpret_cast<float*>(smem + Mp.part);
+  float* stash = reinterpret_cast<float*>(smem + Mp.stash);
+  float* par = reinterpret_cast<float*>(smem + Mp.par);
+  float* wfirst = reinterpret_cast<float*>(smem + Mp.wfirst);
+  float* wlast = reinterpret_cast<float*>(smem + Mp.wlast);
+  double* pro = reinterpret_cast<double*>(smem + Mp.pro);
+  double* red = reinterpret_cast<double*>(smem + Mp.red);
+  auto xch = [&](int p) { return reinterpret_cast<float*>(smem + Mp.xch + p * Mp.xch_stride); };
+
+  // ---- sweep lane layout: lane l of a group owns v nodes [8 l, 8 l + 8)
+  const int lig = tid & (LG - 1);
+  const int grp = tid / LG;
+  const bool pos = lig >= HALF;
+  const bool first_lane = lig == 0, last_lane = lig == LG - 1;
+  const int wbase = (tid & 31) - lig;
+  const int src_left = wbase + (lig > 0 ? lig - 1 : 0);
+  const int src_right = wbase + (lig < LG - 1 ? lig + 1 : LG - 1);
+  const int i0 = grp * R;
+  const unsigned ch0 = 4u * lig, ch1 = 4u * (LG + lig);   // chunk offsets in a column (floats)
+
+  // per-node constants: alpha = a - b|v|/dx, beta = b|v|/dx, M, v M, w v
+  float al[VPT], be[VPT], Mj[VPT], xM[VPT], wv[VPT];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int j = VPT * lig + k;
+    be[k] = A.fb * A.vtab_f[0 * nv + j];
+    al[k] = A.fa - be[k];
+    Mj[k] = A.vtab_f[1 * nv + j];
+    xM[k] = A.vtab_f[2 * nv + j];
+    wv[k] = A.vtab_f[3 * nv + j];
+  }
+  const float f_b = A.fb, f_inv_dx = A.f_inv_dx, f_inv_dv = A.f_inv_dv;
+  const float f_kflux = A.f_kflux, f_dx = A.f_dx, f_inv_nx = A.f_inv_nx;
+
+  auto col = [&](int i) { return g + (unsigned)i * (unsigned)nv; };
+  auto ldcol = [&](float (&v)[VPT], const float* c) {
+    const float4 p = ld4(c + ch0), q = ld4(c + ch1);
+    v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+    v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+  };
+  auto stcol = [&](float* c, const float (&v)[VPT]) {
+    st4(c + ch0, make_float4(v[0], v[1], v[2], v[3]));
+    st4(c + ch1, make_float4(v[4], v[5], v[6], v[7]));
+  };
+  // partial moment <w v g> of one lane
+  auto lane_partial = [&](const float (&v)[VPT]) {
+    float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < VPT; k += 2) {
+      p0 = __fmaf_rn(wv[k], v[k], p0);
+      p1 = __fmaf_rn(wv[k + 1], v[k + 1], p1);
+    }
+    return p0 + p1;
+  };
+  auto put_partial = [&](int i, float p) { part[(unsigned)i * LG + lig] = p; };
+
+  // ------------------------------------------------------------ entry ---
+  const size_t sbase = (size_t)st * nx;
+  const float* gin = reinterpret_cast<const float*>(A.g_in) + sbase * nv;
+  // own columns, and (cluster) the two neighbour columns of step 0
+  for (int i = grp; i < n; i += NGRP) {
+    const float* s = gin + (size_t)(a + i) * nv + VPT * lig;
+    const float4 p = *reinterpret_cast<const float4*>(s), q = *reinterpret_cast<const float4*>(s + 4);
+    st4(col(i) + ch0, p);
+    st4(col(i) + ch1, q);
+  }
+  if (C > 1 && grp < 2) {
+    const int gi = grp == 0 ? (a + nx - 1) % nx : (a + n) % nx;
+    const float* s = gin + (size_t)gi * nv + VPT * lig;
+    float* d = halo + (unsigned)(grp) * nv;  // parity 0: [left, right]
+    st4(d + ch0, *reinterpret_cast<const float4*>(s));
+    st4(d + ch1, *reinterpret_cast<const float4*>(s + 4));
+  }
+
+  // density, rho_bar and the entry field (prefix sum in double)
+  const double* rin = A.rho_in + sbase;
+  const double rc = has_cell ? rin[a + tid] : 0.0;
+  double rb = A.rho_bar;
+  if (isnan(rb)) {
+    double tot;
+    block_scan_d(rc, red, &tot);
+    if (tid == 0)
+      for (int q = 0; q < C; ++q) (C > 1 ? remote(pro, q) : pro)[4 * r] = tot;
+    cluster_or_block_sync(C);
+    double s = 0.0;
+    for (int q = 0; q < C; ++q) s += pro[4 * q];
+    rb = s / nx;
+    cluster_or_block_sync(C);  // pro is reused below
+  }
+  ff rho = ff_from_double(rc), E;
+  {
+    const double d = has_cell ? (rc - rb) * A.dx : 0.0;
+    double t1, t2;
+    const double S = block_scan_d(d, red, &t1);
+    block_scan_d(has_cell ? (double)(nx - (a + tid)) * d : 0.0, red, &t2);
+    if (tid == 0)
+      for (int q = 0; q < C; ++q) {
+        double* dst = C > 1 ? remote(pro, q) : pro;
+        dst[4 * r + 1] = t1;
+        dst[4 * r + 2] = t2;
+      }
+    cluster_or_block_sync(C);
+    double base = 0.0, mean = 0.0;
+    for (int q = 0; q < C; ++q) {
+      if (q < r) base += pro[4 * q + 1];
+      mean += pro[4 * q + 2];
+    }
+    E = ff_from_double(base + S - mean / nx);
+  }
+  // ghost density of the first cell of the right neighbour (cluster)
+  ff ghost = ff_from_double(C > 1 && tid == n - 1 ? rin[(a + n) % nx] : 0.0);
+
+  // partials of g^0
+  for (int i = grp; i < n; i += NGRP) {
+    float v[VPT];
+    ldcol(v, col(i));
+    put_partial(i, lane_partial(v));
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------ macro phases ---
+  float Fc = 0.f, mp = 0.f, mm = 0.f;   // flux, m+, m- of this thread's interface
+
+  // (i): from the partials of the new g; F = 0 at entry (no update)
+  auto macro_i = [&](int p, bool with_flux) {
+    if (w < nwc) {
+      const float* pp = part + (unsigned)tid * LG;
+      // m-: negative-velocity lanes, m+: positive ones; the total flux by
+      // compensated (two-sum) accumulation in two independent chains
+      float sp = 0.f, sm = 0.f, cs[2] = {0.f, 0.f}, ce[2] = {0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < LG; q += (LG >= 4 ? 4 : 2)) {
+        float t[4];
+        if constexpr (LG >= 4) {
+          const float4 v4 = ld4(pp + q);
+          t[0] = v4.x; t[1] = v4.y; t[2] = v4.z; t[3] = v4.w;
+        } else {
+          const float2 v2 = *reinterpret_cast<const float2*>(pp + q);
+          t[0] = v2.x; t[1] = v2.y;
+        }
+#pragma unroll
+        for (int e = 0; e < (LG >= 4 ? 4 : 2); ++e) {
+          if (q + e >= HALF) sp += t[e];
+          else sm += t[e];
+          const ff u = two_sum(cs[e & 1], t[e]);
+          cs[e & 1] = u.hi;
+          ce[e & 1] = __fadd_rn(ce[e & 1], u.lo);
+        }
+      }
+      const ff tot = two_sum(cs[0], cs[1]);
+      const float err = __fadd_rn(__fadd_rn(ce[0], ce[1]), tot.lo);
+      mp = sp;
+      mm = -sm;
+      Fc = with_flux ? __fmaf_rn(tot.hi, f_kflux, __fmul_rn(err, f_kflux)) : 0.f;
+      float ws = Fc;
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, m);
+      float* X = xch(p);
+      if (lane == 0) {
+        st4(wfirst + 4 * w, make_float4(Fc, mm, rho.hi, rho.lo));
+        if (C > 1)
+          for (int q = 0; q < C; ++q) remote(X, q)[4 + r * NW + w] = ws;
+        else
+          X[4 + w] = ws;
+      }
+      if (lane == 31) *reinterpret_cast<float2*>(wlast + 4 * w) = make_float2(Fc, mp);
+      if (C > 1 && tid == 0) *reinterpret_cast<float2*>(remote(X, rl) + 2) = make_float2(Fc, mm);
+      if (C > 1 && tid == n - 1) *reinterpret_cast<float2*>(remote(X, rr)) = make_float2(Fc, mp);
+    }
+    // the CTA's first (last) column becomes the right (left) neighbour
+    // column of the left (right) CTA for the next step
+    const int q4 = nv / 4;
+    if (C > 1 && with_flux && tid >= T - 2 * q4) {
+      const int t = tid - (T - 2 * q4);
+      const bool first = t < q4;
+      const int ch = first ? t : t - q4;
+      float* d = remote(halo, first ? rl : rr) + (unsigned)(2 * p + (first ? 1 : 0)) * nv;
+      st4(d + 4 * ch, ld4(col(first ? 0 : n - 1) + 4 * ch));
+    }
+  };
+
+  // (ii): density and field update (when `update`), then J, P and the
+  // sweep constants (when `constants`)
+  auto macro_ii = [&](int p, bool update, bool constants) {
+    if (w >= nwc) return;
+    const float* X = xch(p);
+    // neighbour values: left interface (F, m+), right interface (F, m-, rho)
+    float Fl = __shfl_up_sync(0xffffffffu, Fc, 1);
+    float mpl = __shfl_up_sync(0xffffffffu, mp, 1);
+    float Fr = __shfl_down_sync(0xffffffffu, Fc, 1);
+    float mmr = __shfl_down_sync(0xffffffffu, mm, 1);
+    ff rr_old = ff_shfl_down(rho, 1);
+    if (lane == 0) {
+      float2 v;
+      if (w > 0) v = *reinterpret_cast<const float2*>(wlast + 4 * (w - 1));
+      else if (C > 1) v = *reinterpret_cast<const float2*>(X);
+      else v = *reinterpret_cast<const float2*>(wlast + 4 * (nwc - 1));
+      Fl = v.x;
+      mpl = v.y;
+    }
+    if (lane == 31) {
+      if (w < nwc - 1 || C == 1) {
+        const float4 v = ld4(wfirst + 4 * (w < nwc - 1 ? w + 1 : 0));
+        Fr = v.x;
+        mmr = v.y;
+        rr_old = {v.z, v.w};
+      } else {
+        const float2 v = *reinterpret_cast<const float2*>(X + 2);
+        Fr = v.x;
+        mmr = v.y;
+        rr_old = ghost;
+      }
+    }
+    ff rho_r = rr_old;
+    if (update) {
+      // mean flux over the whole state (same order in every thread and CTA)
+      float s = 0.f;
+      for (int q = lane; q < C * NW; q += 32) s += ((q % NW) < nwc) ? X[4 + q] : 0.f;
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+      const float Fbar = s * f_inv_nx;
+      rho = ff_add_f(ff_add_f(rho, Fl), -Fc);
+      rho_r = ff_add_f(ff_add_f(rr_old, Fc), -Fr);
+      if (C > 1 && tid == n - 1) ghost = rho_r;
+      E = ff_add_f(E, -f_dx * (Fc - Fbar));
+    }
+    if (constants) {
+      const float e = E.hi;
+      const float dr = (rho_r.hi - rho.hi) + (rho_r.lo - rho.lo);
+      const float J = dr * f_inv_dx - e * 0.5f * (rho.hi + rho_r.hi);
+      const float ep = e > 0.f ? e : 0.f, em = e < 0.f ? -e : 0.f;
+      const float* gc = col(tid);  // end values g_0, g_1, g_{nv-2}, g_{nv-1} sit at
+      const float2 e01 = *reinterpret_cast<const float2*>(gc);            // the same
+      const float2 e23 = *reinterpret_cast<const float2*>(gc + nv - 2);  // offsets
+      const float4 en = make_float4(e01.x, e01.y, e23.x, e23.y);
+      const float P = ((mp - mpl) - (mmr - mm)) * f_inv_dx +
+                      0.5f * ((ep * en.z - em * en.w) - (ep * en.x - em * en.y));
+      st4(par + 4u * tid, make_float4(f_b * ep * f_inv_dv, f_b * em * f_inv_dv, f_b * P, f_b * J));
+    }
+  };
+
+  // ---------------------------------------------------------------- sweep --
+  // registers of the ring: P = old column i-1, Q = i, N = i+1, F = i+2
+  float R0[VPT], R1[VPT], R2[VPT], R3[VPT];
+
+  // old first column of the next group: the stash (filled by that group
+  // before the barrier), or the right halo for the CTA's last group
+  auto right_next = [&](int p) -> const float* {
+    if (C > 1 && grp == NGRP - 1) return halo + (unsigned)(2 * p + 1) * nv;
+    return stash + (unsigned)grp * nv;
+  };
+  // before the barrier that precedes the sweep: the ring's first columns,
+  // and this group's old first column into the previous group's stash
+  auto preload = [&](int p) {
+    const float* lc = i0 > 0 ? col(i0 - 1) : (C > 1 ? halo + (unsigned)(2 * p) * nv : col(n - 1));
+    ldcol(R0, lc);
+    ldcol(R1, col(i0));
+    ldcol(R2, col(i0 + 1));
+    ldcol(R3, col(i0 + 2));
+    float* sd = stash + (unsigned)(grp == 0 ? NGRP - 1 : grp - 1) * nv;
+    st4(sd + ch0, make_float4(R1[0], R1[1], R1[2], R1[3]));
+    st4(sd + ch1, make_float4(R1[4], R1[5], R1[6], R1[7]));
+  };
+
+  auto sweep = [&](int p) {
+    const float* rnext = right_next(p);
+    auto body = [&](int k, float (&P)[VPT], float (&Q)[VPT], float (&N)[VPT]) {
+      const int i = i0 + k;
+      const float4 pr = ld4(par + 4u * i);
+      const float ep = pr.x, em = pr.y, bP = pr.z, bJ = pr.w;
+      const float lnb = __shfl_sync(0xffffffffu, Q[VPT - 1], src_left);
+      const float rnb = __shfl_sync(0xffffffffu, Q[0], src_right);
+      float out[VPT];
+      float Hprev = first_lane ? 0.f : __fmaf_rn(ep, lnb, -em * Q[0]);
+      float ps0 = 0.f, ps1 = 0.f;  // two chains: shorter dependency latency
+#pragma unroll
+      for (int q = 0; q < VPT; ++q) {
+        const float nxt = q < VPT - 1 ? Q[q < VPT - 1 ? q + 1 : q] : rnb;
+        float H = __fmaf_rn(ep, Q[q], -em * nxt);
+        if (q == VPT - 1 && last_lane) H = 0.f;
+        const float u = pos ? P[q] : N[q];
+        const float K = __fmaf_rn(-bJ, xM[q], bP * Mj[q]);
+        float t = __fmaf_rn(al[q], Q[q], K);
+        t = __fmaf_rn(be[q], u, t);
+        t = t - (H - Hprev);
+        Hprev = H;
+        out[q] = t;
+        if (q & 1) ps1 = __fmaf_rn(wv[q], t, ps1);
+        else ps0 = __fmaf_rn(wv[q], t, ps0);
+      }
+      stcol(col(i), out);
+      put_partial(i, ps0 + ps1);
+      // bring in old column i + 3 (the next group's, from the stash, at the
+      // end of the run) into the slot of column i - 1
+      if (k + 3 <= R) ldcol(P, k + 3 < R ? col(i + 3) : rnext);
+    };
+    for (int k = 0; k < R; k += 4) {
+      body(k + 0, R0, R1, R2);
+      body(k + 1, R1, R2, R3);
+      body(k + 2, R2, R3, R0);
+      body(k + 3, R3, R0, R1);
+    }
+  };
+
+  // ------------------------------------------------------------ step loop --
+  macro_i(0, false);
+  cluster_or_block_sync(C);
+  macro_ii(0, false, true);
+  preload(0);
+  __syncthreads();
+  for (int64_t s = 0; s < A.n_steps; ++s) {
+    const int pc = (int)(s & 1), pn = pc ^ 1;  // this step's buffers, the next step's
+    sweep(pc);
+    __syncthreads();
+    macro_i(pn, true);
+    cluster_or_block_sync(C);
+    const bool last = s + 1 == A.n_steps;
+    macro_ii(pn, true, !last);
+    if (!last) preload(pn);
+    __syncthreads();
+  }
+
+  // -------------------------------------------------------------- exit ---
+  int bad = 0;
+  if (has_cell) {
+    const double rv = ff_to_double(rho);
+    A.rho_out[sbase + a + tid] = rv;
+    if (!isfinite(rv)) bad = 1;
+    if (A.mask_out) A.mask_out[sbase + a + tid] = 1;
+  }
+  float* gout = reinterpret_cast<float*>(A.g_buf0) + sbase * nv;
+  for (int i = grp; i < n; i += NGRP) {
+    float* d = gout + (size_t)(a + i) * nv + VPT * lig;
+    *reinterpret_cast<float4*>(d) = ld4(col(i) + ch0);
+    *reinterpret_cast<float4*>(d + 4) = ld4(col(i) + ch1);
+  }
+  if (bad) atomicExch(A.status, (int)MM_ERR_UNSTABLE);
+  if (tid == 0 && r == 0 && A.kin_count)
+    atomicAdd(A.kin_count, (unsigned long long)A.n_steps * (unsigned long long)nx * (unsigned long long)nv);
+}
+
+}  // namespace
+
+// Cluster size and shared-memory bytes of the resident kernel for one state
+// shape, or 0 when the shape is not supported (the streaming kernel then
+// runs).  Requirements: FP32 g, every cell kinetic, one flux per interface,
+// nv = 8 * lanes with lanes in {2, 4, 8, 16, 32}, the cells of a CTA a
+// multiple of 32 and at most 256 (one per thread), and runs of a multiple of
+// 4 columns for each of the 256 / lanes lane groups.
+int fine_resident_cluster(int nx, int nv, bool fp32, bool adapt, int flux_rule, size_t* smem) {
+  if (!fp32 || adapt || flux_rule != 0) return 0;
+  if (nv % VPT) return 0;
+  const int lanes = nv / VPT;
+  if (lanes < 2 || lanes > 32 || (lanes & (lanes - 1))) return 0;
+  // prefer the smallest cluster whose CTAs fit two to an SM (one CTA's
+  // sweep then overlaps the other's latency-bound macro phase), else the
+  // smallest that fits at all
+  for (const unsigned limit : {115712u, 232448u}) {
+    for (int C = 1; C <= 8; C <<= 1) {
+      if (nx % C) break;
+      const int n = nx / C;
+      if (n % 32 || n > T || n % (T / lanes) || (n / (T / lanes)) % 4) continue;
+      const unsigned bytes = res_map(n, nv, lanes, C).total;
+      if (bytes <= limit) {
+        *smem = bytes;
+        return C;
+      }
+    }
+  }
+  return 0;
+}
+
+template <int LG>
+static cudaError_t launch_res(const FineArgs& a, int C, size_t smem, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.batch * C);
+  cfg.blockDim = dim3(T);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = C > 1 ? 1 : 0;  // C == 1: a plain launch
+  return cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG>, a, C);
+}
+
+cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s) {
+  FineArgs a = args;
+  fine_args_floats(a);
+  switch (a.nv / VPT) {
+    case 2: return launch_res<2>(a, C, smem, s);
+    case 4: return launch_res<4>(a, C, smem, s);
+    case 8: return launch_res<8>(a, C, smem, s);
+    case 16: return launch_res<16>(a, C, smem, s);
+    case 32: return launch_res<32>(a, C, smem, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mmk

@@ -11,6 +11,7 @@
 namespace mmk {
 
 constexpr int kFineThreads = 512;   // threads of one fine CTA (one state)
+constexpr int kResThreads = 256;    // threads of one CTA of the resident kernel
 constexpr int kVTabFields = 6;      // per velocity node: |v|/dx, M, v M, w v, w, v
 
 // Velocity constants of one context, built on the host in double.
@@ -50,7 +51,25 @@ struct FineArgs {
   int col_in_smem;      // 1: column arrays in shared memory
   unsigned long long* kin_count;  // kinetic cell-updates (summed)
   int* status;          // device status word (mm_status)
+  // float copies of the scalars, rounded once on the host so that no FP64
+  // instruction is needed (or re-issued) inside the FP32 kernels' step loop
+  float fa, fb, f_dx, f_inv_dx, f_inv_dv, f_kflux, f_fflux, f_inv_nx;
+  float f_dx_lo, f_inv_nx_lo;  // low parts of dx and 1/nx as float-float
 };
+
+// Fill the float copies of a FineArgs from its double fields.
+inline void fine_args_floats(FineArgs& a) {
+  a.fa = (float)a.a;
+  a.fb = (float)a.b;
+  a.f_dx = (float)a.dx;
+  a.f_dx_lo = (float)(a.dx - (double)a.f_dx);
+  a.f_inv_dx = (float)a.inv_dx;
+  a.f_inv_dv = (float)a.inv_dv;
+  a.f_kflux = (float)(a.dt_dx * a.inv_eps);
+  a.f_fflux = (float)(-a.dt_dx * a.m2);
+  a.f_inv_nx = (float)(1.0 / a.nx);
+  a.f_inv_nx_lo = (float)(1.0 / a.nx - (double)a.f_inv_nx);
+}
 
 // Column-array footprint of one state (bytes), for the chosen precision.
 size_t fine_column_bytes(int nx, int nv, int lanes, bool fp32, bool adapt);
@@ -59,6 +78,12 @@ size_t fine_smem_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool co
 // Launch the fine kernel for a batch (one CTA per state).
 cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem,
                         cudaStream_t s);
+
+// Resident variant of F (g kept in shared memory across the whole launch,
+// one thread-block cluster per state).  fine_resident_cluster returns the
+// cluster size (0: shape not supported) and the dynamic shared memory.
+int fine_resident_cluster(int nx, int nv, bool fp32, bool adapt, int flux_rule, size_t* smem);
+cudaError_t launch_fine_resident(const FineArgs& a, int C, size_t smem, cudaStream_t s);
 
 // Arguments of the macroscopic kernels (coarse step, lift, correction).
 struct MacroArgs {

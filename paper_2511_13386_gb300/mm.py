@@ -44,7 +44,7 @@ class mm_params(ctypes.Structure):
                 ("r_scale", ctypes.c_int32), ("flux_rule", ctypes.c_int32), ("dt", ctypes.c_double),
                 ("cfl_theta", ctypes.c_double), ("coarse_kind", ctypes.c_int32),
                 ("coarse_steps", ctypes.c_int32), ("lift_order", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("fine_kernel", ctypes.c_int32)]
 
 
 class mm_alloc(ctypes.Structure):

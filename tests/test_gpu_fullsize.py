@@ -16,14 +16,15 @@ pytestmark = pytest.mark.gpu
 N_STATES = 128
 
 
-@pytest.mark.parametrize("prec", [mm.MM_FP32G, mm.MM_FP64])
-def test_full_slice_all_states_sampled(prec):
+@pytest.mark.parametrize("prec,kernel", [(mm.MM_FP32G, 2), (mm.MM_FP32G, 1), (mm.MM_FP64, 0)],
+                         ids=["fp32-resident", "fp32-streaming", "fp64"])
+def test_full_slice_all_states_sampled(prec, kernel):
     dev = device()
     w = W.batched()
     rho_b, g_b = w.with_batch(8)
     rho = np.tile(rho_b, (N_STATES // 8, 1))
     g = np.tile(g_b, (N_STATES // 8, 1, 1))
-    p = params(w.nx, w.nv, w.eps, prec, rho_bar=1.0)
+    p = params(w.nx, w.nv, w.eps, prec, rho_bar=1.0, fine_kernel=kernel)
     ctx = mm.mm_create(p)
     span = w.t_end / w.n_slices
     q = mm.mm_query(ctx, span)
