@@ -58,7 +58,14 @@ constexpr int VPT = 8;  // velocity nodes per lane (two 16-byte chunks)
 // Shared-memory map (byte offsets).  g columns are stored with the lane's
 // two 16-byte chunks interleaved across the group (chunk q of lane l at
 // (q * LG + l) * 16), so that eight consecutive lanes touch 128 contiguous
-// bytes per access and no bank is hit twice.
+// bytes per access and no bank is hit twice.  The per-column partial moments
+// (one row per lane) and the four end values g_0, g_1, g_{nv-2}, g_{nv-1}
+// (four more rows) are stored transposed with a row stride of n + 1 floats:
+// a group writes one column of it, a thread of the macro phase reads one
+// row entry per value, both without bank conflicts.  The per-interface sweep
+// constants are stored with one 16-byte pad after each run of R columns, so
+// that the groups of a warp, which read the same position of their runs at
+// once, hit different banks.
 struct ResMap {
   unsigned g, halo, stash, part, par, wfirst, wlast, xch, pro, red, total;
   unsigned xch_stride;  // bytes per parity in xch
@@ -71,9 +78,9 @@ __host__ __device__ inline ResMap res_map(int n, int nv, int lanes, int C) {
   unsigned o = 0;
   m.g = o;      o = up16(o + 4u * n * nv);
   m.halo = o;   o = up16(o + 4u * 4 * nv);          // [parity][left, right][nv]
-  m.part = o;   o = up16(o + 4u * n * lanes);
+  m.part = o;   o = up16(o + 4u * (lanes + 4) * (n + 1));  // [lanes + 4][n + 1], see below
   m.stash = o;  o = up16(o + 4u * (T / lanes) * nv);  // per group: next group's old first column
-  m.par = o;    o = up16(o + 16u * n);
+  m.par = o;    o = up16(o + 16u * (n + n / ((unsigned)n / (T / lanes))));  // padded, see below
   m.wfirst = o; o = up16(o + 16u * NW);             // per warp: F, m-, rho.hi, rho.lo
   m.wlast = o;  o = up16(o + 16u * NW);             // per warp: F, m+
   m.xch_stride = up16(16u + 4u * C * NW);           // xL(F, m+), xR(F, m-), sums
@@ -135,6 +142,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   const int nwc = n >> 5;                // warps that own cells
   const bool has_cell = tid < n;
   const int R = n / NGRP;                // columns per group
+  const bool warp_local = R == LG;       // thread t's cell t lies in its own group's run
 
   const ResMap Mp = res_map(n, nv, LG, C);
   float* g = reinterpret_cast<float*>(smem + Mp.g);
@@ -193,7 +201,18 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
     }
     return p0 + p1;
   };
-  auto put_partial = [&](int i, float p) { part[(unsigned)i * LG + lig] = p; };
+  const unsigned PS = n + 1;  // row stride of part
+  auto put_partial = [&](int i, float p, const float (&v)[VPT]) {
+    part[lig * PS + i] = p;
+    if (first_lane) {
+      part[(LG + 0) * PS + i] = v[0];
+      part[(LG + 1) * PS + i] = v[1];
+    }
+    if (last_lane) {
+      part[(LG + 2) * PS + i] = v[VPT - 2];
+      part[(LG + 3) * PS + i] = v[VPT - 1];
+    }
+  };
 
   // ------------------------------------------------------------ entry ---
   const size_t sbase = (size_t)st * nx;
@@ -255,7 +274,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   for (int i = grp; i < n; i += NGRP) {
     float v[VPT];
     ldcol(v, col(i));
-    put_partial(i, lane_partial(v));
+    put_partial(i, lane_partial(v), v);
   }
   __syncthreads();
 
@@ -265,28 +284,20 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   // (i): from the partials of the new g; F = 0 at entry (no update)
   auto macro_i = [&](int p, bool with_flux) {
     if (w < nwc) {
-      const float* pp = part + (unsigned)tid * LG;
+      const float* pp = part + tid;
       // m-: negative-velocity lanes, m+: positive ones; the total flux by
       // compensated (two-sum) accumulation in two independent chains
       float sp = 0.f, sm = 0.f, cs[2] = {0.f, 0.f}, ce[2] = {0.f, 0.f};
+      float t[LG];
 #pragma unroll
-      for (int q = 0; q < LG; q += (LG >= 4 ? 4 : 2)) {
-        float t[4];
-        if constexpr (LG >= 4) {
-          const float4 v4 = ld4(pp + q);
-          t[0] = v4.x; t[1] = v4.y; t[2] = v4.z; t[3] = v4.w;
-        } else {
-          const float2 v2 = *reinterpret_cast<const float2*>(pp + q);
-          t[0] = v2.x; t[1] = v2.y;
-        }
+      for (int q = 0; q < LG; ++q) t[q] = pp[q * PS];
 #pragma unroll
-        for (int e = 0; e < (LG >= 4 ? 4 : 2); ++e) {
-          if (q + e >= HALF) sp += t[e];
-          else sm += t[e];
-          const ff u = two_sum(cs[e & 1], t[e]);
-          cs[e & 1] = u.hi;
-          ce[e & 1] = __fadd_rn(ce[e & 1], u.lo);
-        }
+      for (int q = 0; q < LG; ++q) {
+        if (q >= HALF) sp += t[q];
+        else sm += t[q];
+        const ff u = two_sum(cs[q & 1], t[q]);
+        cs[q & 1] = u.hi;
+        ce[q & 1] = __fadd_rn(ce[q & 1], u.lo);
       }
       const ff tot = two_sum(cs[0], cs[1]);
       const float err = __fadd_rn(__fadd_rn(ce[0], ce[1]), tot.lo);
@@ -310,13 +321,25 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
     }
     // the CTA's first (last) column becomes the right (left) neighbour
     // column of the left (right) CTA for the next step
-    const int q4 = nv / 4;
-    if (C > 1 && with_flux && tid >= T - 2 * q4) {
-      const int t = tid - (T - 2 * q4);
-      const bool first = t < q4;
-      const int ch = first ? t : t - q4;
-      float* d = remote(halo, first ? rl : rr) + (unsigned)(2 * p + (first ? 1 : 0)) * nv;
-      st4(d + 4 * ch, ld4(col(first ? 0 : n - 1) + 4 * ch));
+    if (C > 1 && with_flux) {
+      if (warp_local) {  // by the groups that wrote them
+        if (grp == 0 || grp == NGRP - 1) {
+          const bool first = grp == 0;
+          const float* c = col(first ? 0 : n - 1);
+          float* d = remote(halo, first ? rl : rr) + (unsigned)(2 * p + (first ? 1 : 0)) * nv;
+          st4(d + ch0, ld4(c + ch0));  // raw chunks: same layout at both ends
+          st4(d + ch1, ld4(c + ch1));
+        }
+      } else {
+        const int q4 = nv / 4;
+        if (tid >= T - 2 * q4) {
+          const int t = tid - (T - 2 * q4);
+          const bool first = t < q4;
+          const int ch = first ? t : t - q4;
+          float* d = remote(halo, first ? rl : rr) + (unsigned)(2 * p + (first ? 1 : 0)) * nv;
+          st4(d + 4 * ch, ld4(col(first ? 0 : n - 1) + 4 * ch));
+        }
+      }
     }
   };
 
@@ -370,13 +393,11 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
       const float dr = (rho_r.hi - rho.hi) + (rho_r.lo - rho.lo);
       const float J = dr * f_inv_dx - e * 0.5f * (rho.hi + rho_r.hi);
       const float ep = e > 0.f ? e : 0.f, em = e < 0.f ? -e : 0.f;
-      const float* gc = col(tid);  // end values g_0, g_1, g_{nv-2}, g_{nv-1} sit at
-      const float2 e01 = *reinterpret_cast<const float2*>(gc);            // the same
-      const float2 e23 = *reinterpret_cast<const float2*>(gc + nv - 2);  // offsets
-      const float4 en = make_float4(e01.x, e01.y, e23.x, e23.y);
+      const float* pe = part + LG * PS + tid;  // end values of the new column
+      const float4 en = make_float4(pe[0], pe[PS], pe[2 * PS], pe[3 * PS]);
       const float P = ((mp - mpl) - (mmr - mm)) * f_inv_dx +
                       0.5f * ((ep * en.z - em * en.w) - (ep * en.x - em * en.y));
-      st4(par + 4u * tid, make_float4(f_b * ep * f_inv_dv, f_b * em * f_inv_dv, f_b * P, f_b * J));
+      st4(par + 4u * (tid + tid / R), make_float4(f_b * ep * f_inv_dv, f_b * em * f_inv_dv, f_b * P, f_b * J));
     }
   };
 
@@ -407,7 +428,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
     const float* rnext = right_next(p);
     auto body = [&](int k, float (&P)[VPT], float (&Q)[VPT], float (&N)[VPT]) {
       const int i = i0 + k;
-      const float4 pr = ld4(par + 4u * i);
+      const float4 pr = ld4(par + 4u * (i + grp));  // padded: i / R == grp
       const float ep = pr.x, em = pr.y, bP = pr.z, bJ = pr.w;
       const float lnb = __shfl_sync(0xffffffffu, Q[VPT - 1], src_left);
       const float rnb = __shfl_sync(0xffffffffu, Q[0], src_right);
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
         else ps0 = __fmaf_rn(wv[q], t, ps0);
       }
       stcol(col(i), out);
-      put_partial(i, ps0 + ps1);
+      put_partial(i, ps0 + ps1, out);
       // bring in old column i + 3 (the next group's, from the stash, at the
       // end of the run) into the slot of column i - 1
       if (k + 3 <= R) ldcol(P, k + 3 < R ? col(i + 3) : rnext);
@@ -452,7 +473,12 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   for (int64_t s = 0; s < A.n_steps; ++s) {
     const int pc = (int)(s & 1), pn = pc ^ 1;  // this step's buffers, the next step's
     sweep(pc);
-    __syncthreads();
+    // when every group's run is as long as the group is wide, thread t owns
+    // cell t, which its own group swept: the partials it sums are the
+    // group's (a warp barrier suffices) and the warps run on into macro (i)
+    // without waiting for each other
+    if (warp_local) __syncwarp();
+    else __syncthreads();
     macro_i(pn, true);
     cluster_or_block_sync(C);
     const bool last = s + 1 == A.n_steps;
