@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NX, NV, EPS, T_END, N_SLICES = 1024, 64, 1e-2, 1.0, 128
-FLOPS_PER_UPDATE = 20       # algorithmic FP32 flops per cell-update
+FLOPS_PER_UPDATE = 16       # algorithmic FP32 flops per cell-update (an FMA counts 2)
 BYTES_PER_UPDATE = 8        # algorithmic HBM bytes per FP32 cell-update (read g, write g)
 
 
@@ -96,6 +96,39 @@ def kernel_only(a):
         torch.cuda.synchronize()
         print(json.dumps({"kernel": "coarse chain", "ms": 1e3 * (time.perf_counter() - t0) / a.steps}))
     ctx.close()
+
+
+# ---------------------------------------------------------------- profiles --
+
+PROFILE = os.path.join(ROOT, "profiles", "fine_resident_kernel__batched_nx1024_nv64_fp32.md")
+KERNEL_SOURCES = ["paper_2511_13386_gb300/csrc/mm_fine_resident.cu", "paper_2511_13386_gb300/csrc/ff.cuh",
+                  "paper_2511_13386_gb300/csrc/mm_internal.h"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fine kernel from the committed ncu
+    summary, or None when the summary is missing or the kernel's sources
+    changed since it was taken."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("traffic_bytes_per_launch:",
+                                                                                 "kernel_source_sha256:")))
+    if fields.get("kernel_source_sha256", "").strip() != kernel_source_hash():
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
 
 
 # ----------------------------------------------------------------- oracle --
@@ -267,10 +300,13 @@ def run_ours(a, rank, world, dist):
     achieved_flops = FLOPS_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e12
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alg_gbs = BYTES_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e9
+    kname = (f"fine_resident_kernel<{q['lanes']}> (cluster of {q['cluster']})" if q["fine_kernel"] == 2
+             else f"fine_kernel<{'float' if prec == mm.MM_FP32G else 'double'},{q['vpt']}>")
     roofline = {"bound": "alu", "achieved": round(achieved_flops, 3), "peak": round(fp32_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved_flops / fp32_peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved_flops / fp32_peak, 4),
+                "traffic": profiled_traffic() if q["fine_kernel"] == 2 else None,
                 "peak_source": f"FP32 FMA lanes x clock: {n_sm} SMs x 128 x 2 x {sm_mhz:.0f} MHz",
-                "kernel": "fine_kernel<float,8>", "launch_ms": round(fine_launch_ms, 3),
+                "kernel": kname, "launch_ms": round(fine_launch_ms, 3),
                 "hbm_equivalent": {"achieved_gbs": round(alg_gbs, 1), "peak_gbs": hbm_peak,
                                    "frac_of_measured": round(alg_gbs / hbm_peak, 3)}}
     ctx.close()

@@ -138,6 +138,9 @@ typedef struct {
   size_t state_bytes;    /* bytes of one (rho, g) slice state */
   int32_t vpt;           /* velocity nodes per lane in the fine kernel */
   int32_t lanes;         /* lanes per interface column in the fine kernel */
+  int32_t fine_kernel;   /* F implementation mm_fine_propagate runs:
+                            1 = streaming, 2 = resident */
+  int32_t cluster;       /* CTAs per state (thread-block cluster size) */
 } mm_info;
 
 typedef struct {

@@ -301,6 +301,12 @@ extern "C" mm_status mm_query(const mm_ctx* c, double t_span, mm_info* out) {
   out->state_bytes = (size_t)c->p.nx * 8 + (size_t)c->p.nx * c->p.nv * gsz;
   out->vpt = c->lay.vpt;
   out->lanes = c->lay.lanes;
+  size_t sm;
+  const int C = c->p.fine_kernel == 1 ? 0
+                                      : mmk::fine_resident_cluster(c->p.nx, c->p.nv, c->p.precision == MM_FP32G,
+                                                                   c->p.adapt != 0, c->p.flux_rule, &sm);
+  out->fine_kernel = C ? 2 : 1;
+  out->cluster = C ? C : 1;
   return MM_OK;
 }
 

@@ -54,7 +54,8 @@ class mm_alloc(ctypes.Structure):
 class mm_info(ctypes.Structure):
     _fields_ = [("dt_limit", ctypes.c_double), ("dt", ctypes.c_double), ("n_steps", ctypes.c_int64),
                 ("m2", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
-                ("state_bytes", ctypes.c_size_t), ("vpt", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+                ("state_bytes", ctypes.c_size_t), ("vpt", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("fine_kernel", ctypes.c_int32), ("cluster", ctypes.c_int32)]
 
 
 class mm_fine_stats(ctypes.Structure):
