@@ -275,6 +275,55 @@ MM_API mm_status parareal_run(mm_ctx* ctx, const mm_parareal_cfg* cfg,
                        double* rho_slices_out, mm_parareal_stats* stats,
                        void* stream);
 
+/* --------------------------------------------------------- many solves --- */
+
+/* A batch of independent parareal solves (Algorithm 1, Sec. 3.3) of any
+   shapes, advanced together: each mm_batch_step runs one parareal iteration
+   of every unfinished solve in three launches -- the coarse guess of newly
+   added solves (one CTA per solve), every fine propagation F the iteration
+   needs, of all solves and slices, as one work list walked by a persistent
+   kernel (longest items first; each item lifts its slice density in place,
+   so no per-slice perturbation is stored), and the sequential corrections
+   with their successive errors (one CTA per solve).  Solves may be added
+   between steps; a finished solve stays until taken.  The F of a batch is
+   the streaming kernel (FP32 g with 8 velocity nodes per lane, or FP64 with
+   4: nv / 16, resp. nv / 8, a whole number of lanes, at most 32 lanes).
+   Results equal parareal_run's to rounding (the lifting inside the fine
+   kernel sums the field in another order) and do not depend on the other
+   solves of the batch.  Not thread-safe. */
+typedef struct mm_batch mm_batch;
+
+/* Device bytes a solve holds while in a batch (the slice densities, the
+   fine results, the previous coarse values and slice 0's perturbation). */
+MM_API size_t mm_batch_footprint(const mm_params* p, const mm_parareal_cfg* cfg);
+MM_API mm_status mm_batch_create(const mm_alloc* alloc, mm_batch** out);
+/* Copy a solve's initial data (host or device arrays rho0 [nx], g0 [nx][nv]
+   in the params' precision) into the batch.  Errors: MM_ERR_INVALID
+   (parameters, configuration, unsupported nv), MM_ERR_OOM, MM_ERR_CUDA. */
+MM_API mm_status mm_batch_add(mm_batch* b, const mm_params* p, const mm_parareal_cfg* cfg,
+                       const double* rho0, const void* g0, uint64_t* id);
+/* One parareal iteration of every unfinished solve; *active (nullable)
+   receives the number of solves that were unfinished before the step.
+   Synchronises the stream.  Errors: MM_ERR_UNSTABLE (non-finite density),
+   MM_ERR_CUDA, MM_ERR_OOM. */
+MM_API mm_status mm_batch_step(mm_batch* b, int32_t* active, void* stream);
+MM_API mm_status mm_batch_query(mm_batch* b, uint64_t id, int32_t* done);
+/* Copy a finished solve's slice densities [n_slices + 1][nx] (host or
+   device; NULL to discard) and statistics, and release it.
+   Errors: MM_ERR_NOT_READY, MM_ERR_UNKNOWN_TICKET. */
+MM_API mm_status mm_batch_take(mm_batch* b, uint64_t id, double* rho_slices_out,
+                        mm_parareal_stats* stats);
+MM_API size_t mm_batch_bytes(const mm_batch* b);
+MM_API void mm_batch_destroy(mm_batch* b);
+
+/* parareal_run for n solves at once through a batch: rho0[q], g0[q],
+   rho_slices_out[q] are solve q's arrays (host or device); stats may be
+   NULL or an array of n.  Errors: as mm_batch_add / mm_batch_step. */
+MM_API mm_status parareal_run_many(int32_t n, const mm_params* params, const mm_parareal_cfg* cfgs,
+                            const double* const* rho0, const void* const* g0,
+                            double* const* rho_slices_out, mm_parareal_stats* stats,
+                            void* stream);
+
 /* ------------------------------------------------------------ serving --- */
 
 typedef struct mm_server mm_server;

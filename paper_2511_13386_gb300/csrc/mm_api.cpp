@@ -407,6 +407,7 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.mask_out = (uint8_t*)d_mask;
   a.vtab = c->d_vtab;
   a.vtab_f = c->d_vtab_f;
+  a.xiM = c->vg.xiM;
 
   const size_t colb = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt);
   const bool in_smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, true) <= 232448;
@@ -769,8 +770,65 @@ mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out)
   a.r_fac = p.r_scale ? p.eps * p.eps : 1.0;
   a.vtab = c->d_vtab;
   a.vtab_f = c->d_vtab_f;
+  a.xiM = c->vg.xiM;
   a.col_in_smem = f.col_in_smem ? 1 : 0;
   a.col_ws_stride = f.col_in_smem ? 0 : f.col_bytes;
   *out = f;
   return MM_OK;
+}
+
+// ------------------------------------------- context access for batches --
+
+const mm_params& mmk::ctx_params(const mm_ctx* c) { return c->p; }
+int mmk::ctx_device(const mm_ctx* c) { return c->device; }
+int64_t mmk::ctx_fine_steps(const mm_ctx* c, double span) { return steps_for(span, c->dt_limit); }
+mmk::MacroArgs mmk::ctx_macro_args(const mm_ctx* c, double span, double rho_bar) {
+  return macro_args(c, 1, span, rho_bar);
+}
+double mmk::ctx_mean(const double* rho, int nx) {
+  double m = 0.0;
+  for (int i = 0; i < nx; ++i) m += rho[i];
+  return m / nx;
+}
+
+mmk::FineArgs mmk::ctx_fine_args(const mm_ctx* c, int64_t n, double dt, double rho_bar) {
+  const mm_params& p = c->p;
+  FineArgs a{};
+  a.nx = p.nx;
+  a.nv = p.nv;
+  a.batch = 1;
+  a.n_steps = n;
+  a.lanes = c->lay.lanes;
+  a.nh = c->lay.nh;
+  a.nhp = c->lay.nhp;
+  a.dt = dt;
+  a.dx = p.x_len / p.nx;
+  a.inv_dx = 1.0 / a.dx;
+  a.inv_dv = 1.0 / c->vg.dv;
+  a.eps = p.eps;
+  a.inv_eps = 1.0 / p.eps;
+  a.a = exp(-dt / (p.eps * p.eps));
+  a.b = p.eps * (1.0 - a.a);
+  a.m2 = c->vg.m2;
+  a.dt_dx = dt / a.dx;
+  a.rho_bar = rho_bar;
+  a.adapt = p.adapt;
+  a.r_scale = p.r_scale;
+  a.flux_rule = p.flux_rule;
+  a.thr_g = p.thr_g;
+  a.thr_R = p.thr_R;
+  a.r_fac = p.r_scale ? p.eps * p.eps : 1.0;
+  a.vtab = c->d_vtab;
+  a.vtab_f = c->d_vtab_f;
+  a.xiM = c->vg.xiM;
+  fine_args_floats(a);
+  return a;
+}
+
+// The lane layout a work list runs with: 8 nodes per lane in FP32, 4 in FP64
+// (the persistent kernel is compiled for those only).
+bool mmk::ctx_list_layout(const mm_ctx* c, int* lanes) {
+  const bool fp32 = c->p.precision == MM_FP32G;
+  *lanes = c->lay.lanes;
+  return c->lay.vpt == (fp32 ? 8 : 4);
 }

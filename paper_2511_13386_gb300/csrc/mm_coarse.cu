@@ -181,8 +181,8 @@ struct Scratch {
   double *w, *s0, *s1, *s2, *s3, *s4, *rs;
 };
 
-__device__ Scratch scratch_of(unsigned char* smem, double* gws, int nx, int in_smem) {
-  const size_t per = (size_t)kScratchArrays * nx + kReducedDoubles;
+__device__ Scratch scratch_of(unsigned char* smem, double* gws, int nx, int in_smem, size_t per = 0) {
+  if (per == 0) per = (size_t)kScratchArrays * nx + kReducedDoubles;
   double* base = in_smem ? reinterpret_cast<double*>(smem + 1024) : gws + (size_t)blockIdx.x * per;
   return {base, base + nx, base + 2 * nx, base + 3 * nx, base + 4 * nx, base + 5 * nx, base + 6 * nx};
 }
@@ -240,12 +240,9 @@ __global__ void lift_kernel(MacroArgs a, const double* rho, G* g, double* gws, i
 // Sequential correction of Algorithm 1 for one solve (one CTA):
 // for n = k..N-1: Gn = G(rho^{n,k+1}); rho^{n+1,k+1} = F + (Gn - Gprev);
 // Gprev = Gn; err = max |rho^{n+1,k+1} - rho^{n+1,k}|.
-__global__ void correct_kernel(CorrectArgs c, double* gws, int in_smem) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);
+__device__ void correct_solve(const CorrectArgs& c, const Scratch& S, double* red) {
   const MacroArgs& a = c.m;
   const int nx = a.nx;
-  Scratch S = scratch_of(smem, gws, nx, in_smem);
   double emax = 0.0;
   for (int n = c.k; n < c.n_slices; ++n) {
     const double* rn = c.rho + (size_t)n * nx;
@@ -271,15 +268,26 @@ __global__ void correct_kernel(CorrectArgs c, double* gws, int in_smem) {
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) e = fmax(e, red[q]);
     *c.err = e;
   }
+  __syncthreads();
+}
+
+__global__ void correct_kernel(CorrectArgs c, double* gws, int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  correct_solve(c, scratch_of(smem, gws, c.m.nx, in_smem), reinterpret_cast<double*>(smem));
+}
+
+// The correction of many solves, one CTA each (per-CTA scratch of `per`
+// doubles when it does not fit shared memory).
+__global__ void correct_list_kernel(const CorrectArgs* list, double* gws, int in_smem, size_t per) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const CorrectArgs& c = list[blockIdx.x];
+  correct_solve(c, scratch_of(smem, gws, c.m.nx, in_smem, per), reinterpret_cast<double*>(smem));
 }
 
 // Coarse guess of Algorithm 1: rho^{n+1,0} = G(rho^{n,0}), Gprev = rho^{n+1,0}.
-__global__ void coarse_chain_kernel(MacroArgs a, int n_slices, double* rho, double* gprev,
-                                    double* gws, int in_smem) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);
+__device__ void coarse_chain_solve(const MacroArgs& a, int n_slices, double* rho, double* gprev, const Scratch& S,
+                                   double* red) {
   const int nx = a.nx;
-  Scratch S = scratch_of(smem, gws, nx, in_smem);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = rho[i];
   __syncthreads();
   for (int n = 0; n < n_slices; ++n) {
@@ -292,6 +300,21 @@ __global__ void coarse_chain_kernel(MacroArgs a, int n_slices, double* rho, doub
     }
     __syncthreads();
   }
+}
+
+__global__ void coarse_chain_kernel(MacroArgs a, int n_slices, double* rho, double* gprev,
+                                    double* gws, int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  coarse_chain_solve(a, n_slices, rho, gprev, scratch_of(smem, gws, a.nx, in_smem),
+                     reinterpret_cast<double*>(smem));
+}
+
+// The coarse guess of many solves, one CTA each.
+__global__ void coarse_chain_list_kernel(const CorrectArgs* list, double* gws, int in_smem, size_t per) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const CorrectArgs& c = list[blockIdx.x];
+  coarse_chain_solve(c.m, c.n_slices, c.rho, c.gprev, scratch_of(smem, gws, c.m.nx, in_smem, per),
+                     reinterpret_cast<double*>(smem));
 }
 
 // ------------------------------------------------------------- launches --
@@ -333,6 +356,28 @@ cudaError_t launch_lift(const MacroArgs& a, const double* rho, void* g_out, bool
                         cudaStream_t s) {
   if (fp32) return launch_macro(lift_kernel<float>, a.batch, a.nx, gws, s, a, rho, (float*)g_out);
   return launch_macro(lift_kernel<double>, a.batch, a.nx, gws, s, a, rho, (double*)g_out);
+}
+
+size_t macro_list_ws_bytes(int nx_max, int grid) { return macro_ws_bytes(nx_max, grid); }
+
+static cudaError_t launch_list(void (*kernel)(const CorrectArgs*, double*, int, size_t), const CorrectArgs* list,
+                               int n, int nx_max, double* gws, cudaStream_t s) {
+  const bool in_smem = macro_fits(nx_max);
+  const size_t smem = macro_smem(nx_max, in_smem);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e != cudaSuccess) return e;
+  if (!in_smem && gws == nullptr) return cudaErrorInvalidValue;
+  const size_t per = (size_t)kScratchArrays * nx_max + kReducedDoubles;
+  kernel<<<n, kMacroThreads, smem, s>>>(list, gws, in_smem ? 1 : 0, per);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct_list(const CorrectArgs* list, int n, int nx_max, double* gws, cudaStream_t s) {
+  return launch_list(correct_list_kernel, list, n, nx_max, gws, s);
+}
+
+cudaError_t launch_coarse_chain_list(const CorrectArgs* list, int n, int nx_max, double* gws, cudaStream_t s) {
+  return launch_list(coarse_chain_list_kernel, list, n, nx_max, gws, s);
 }
 
 cudaError_t launch_correct(const CorrectArgs& c, double* gws, cudaStream_t s) {

@@ -289,21 +289,84 @@ __device__ __forceinline__ Cols<G> carve(unsigned char* base, int nx, int lanes,
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Lifting of order one (Def. 1, identification l = 0 of Sec. 2.1) of one
+// density into g, by the whole block, in double: the Poisson law of S^MM
+// (prefix sum, mean-zero gauge), J of S^0, then
+// g_{i+1/2,j} = -eps (xi_j M_j - <xi M> M_j) J_{i+1/2}.  E and J use the
+// first 16 nx bytes of `scratch`.
+template <class G>
+__device__ void lift_block(const FineArgs& A, const double* rho, double rb, G* g, unsigned char* scratch,
+                           double* red) {
+  const int nx = A.nx, nv = A.nv, T = blockDim.x, tid = threadIdx.x;
+  double* E = reinterpret_cast<double*>(scratch);
+  double* J = E + nx;
+  const int cpt = (nx + T - 1) / T;
+  const int c0 = min(tid * cpt, nx), c1 = min(c0 + cpt, nx);
+  double t1 = 0.0, t2 = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    const double d = (rho[c] - rb) * A.dx;
+    t1 += d;
+    E[c] = t1;
+    t2 += d * (double)(nx - c);
+  }
+  const int w = tid >> 5, l = tid & 31, nw = T >> 5;
+  double inc = t1;
+  for (int d = 1; d < 32; d <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, inc, d);
+    if (l >= d) inc += t;
+  }
+  double ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (l == 0) ex = 0.0;
+  for (int m = 16; m > 0; m >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, m);
+  __syncthreads();
+  if (l == 31) red[w] = inc;
+  if (l == 0) red[32 + w] = t2;
+  __syncthreads();
+  double off = 0.0, tw = 0.0;
+  for (int q = 0; q < nw; ++q) {
+    if (q < w) off += red[q];
+    tw += red[32 + q];
+  }
+  const double mean = tw * (1.0 / nx), base = off + ex;
+  for (int c = c0; c < c1; ++c) E[c] = base + E[c] - mean;
+  __syncthreads();
+  for (int c = c0; c < c1; ++c) {
+    const double r0 = rho[c], r1 = rho[c + 1 == nx ? 0 : c + 1];
+    J[c] = (r1 - r0) * A.inv_dx - E[c] * 0.5 * (r0 + r1);
+  }
+  __syncthreads();
+  const double* vM = A.vtab + 2 * nv;
+  const double* Mj = A.vtab + 1 * nv;
+  const unsigned n = (unsigned)nx * (unsigned)nv;
+  for (unsigned q = tid; q < n; q += T) {
+    const unsigned i = q / (unsigned)nv, j = q - i * (unsigned)nv;
+    const double Ji = J[i];
+    g[q] = (G)(-A.eps * (vM[j] * Ji - A.xiM * Ji * Mj[j]));
+  }
+  __syncthreads();
+}
+
+// F for one state: n_steps steps from (rin, gin); gin == nullptr lifts the
+// density first.  buf0/buf1 are the two step buffers (the last step writes
+// buf0); colbase holds the column arrays (shared or global memory).
 template <class G, int VPT, bool ADAPT, bool CSMEM>
-__global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A) {
+__device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin, const G* gin, G* buf0, G* buf1,
+                                           double* rout, uint8_t* mout, unsigned char* smem,
+                                           unsigned char* colbase) {
   using M = MP<G>;
   using R = typename M::R;
   using Acc = typename M::A;
-  extern __shared__ __align__(16) unsigned char smem[];
 
   const int tid = threadIdx.x;
-  const int st = blockIdx.x;
   const int nx = A.nx, nv = A.nv, Lg = A.lanes;
   constexpr int T = kFineThreads;
 
   double* red = reinterpret_cast<double*>(smem);
-  unsigned char* colbase = CSMEM ? smem + 8 * kRedSlots
-                                 : reinterpret_cast<unsigned char*>(A.col_ws) + (size_t)st * A.col_ws_stride;
+  if (gin == nullptr) {  // the lifted density goes where the first step does not write
+    G* lifted = (A.n_steps & 1) ? buf1 : buf0;
+    lift_block<G>(A, rin, A.rho_bar, lifted, colbase, red);
+    gin = lifted;
+  }
   Cols<G> C = carve<G>(colbase, nx, Lg, ADAPT);
 
   // ---- ownership of cells in the macro phase
@@ -348,7 +411,6 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
   const R Rdx = M::c(A.dx), Rinv_nx = M::c(1.0 / nx);
 
   // ---- prologue: density, rho_bar, moments of g_in
-  const double* rin = A.rho_in + (size_t)st * nx;
   double rb = A.rho_bar;
   {
     double s = 0.0;
@@ -361,7 +423,6 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
   }
   const R Rrb = M::c(rb);
 
-  const G* gin = reinterpret_cast<const G*>(A.g_in) + (size_t)st * nx * nv;
   for (int i = grp; i < nx; i += ngrp) {
     G w1[VPT];
 #pragma unroll
@@ -595,8 +656,6 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
   };
 
   // --------------------------------------------------------------- sweep --
-  G* buf0 = reinterpret_cast<G*>(A.g_buf0) + (size_t)st * nx * nv;
-  G* buf1 = reinterpret_cast<G*>(A.g_buf1) + (size_t)st * nx * nv;
 
   auto sweep = [&](const G* src, G* dst) {
     const int epg = (count + ngrp - 1) / ngrp;
@@ -698,12 +757,65 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
   int bad = 0;
   for (int c = c0; c < c1; ++c) {
     const double r = M::tod(C.rho[c]);
-    A.rho_out[(size_t)st * nx + c] = r;
+    rout[c] = r;
     if (!isfinite(r)) bad = 1;
-    if (A.mask_out) A.mask_out[(size_t)st * nx + c] = ADAPT ? cell_cur[c] : 1;
+    if (mout) mout[c] = ADAPT ? cell_cur[c] : 1;
   }
   if (bad) atomicExch(A.status, (int)MM_ERR_UNSTABLE);
   if (tid == 0 && A.kin_count) atomicAdd(A.kin_count, (unsigned long long)kin_total * (unsigned long long)nv);
+}
+
+// One CTA per state of a uniform batch.
+template <class G, int VPT, bool ADAPT, bool CSMEM>
+__global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t st = blockIdx.x;
+  const size_t sz = (size_t)A.nx * A.nv;
+  unsigned char* colbase = CSMEM ? smem + 8 * kRedSlots
+                                 : reinterpret_cast<unsigned char*>(A.col_ws) + st * A.col_ws_stride;
+  fine_state<G, VPT, ADAPT, CSMEM>(A, A.rho_in + st * A.nx, reinterpret_cast<const G*>(A.g_in) + st * sz,
+                                   reinterpret_cast<G*>(A.g_buf0) + st * sz,
+                                   reinterpret_cast<G*>(A.g_buf1) + st * sz, A.rho_out + st * A.nx,
+                                   A.mask_out ? A.mask_out + st * A.nx : nullptr, smem, colbase);
+}
+
+// Persistent work-list kernel: each CTA takes (solve, slice) items from a
+// global counter until the list is exhausted (dynamic scheduling of uneven
+// fine propagations; the list is sorted by decreasing cost on the host).
+// An item propagates rho^{n,k} of its solve (g from slice 0's data, or
+// lifted from the density) and writes F(rho)^{n+1}.  The step buffers and
+// (when they do not fit shared memory) the column arrays are per-CTA
+// workspace reused from item to item.
+template <class G, int VPT, bool ADAPT, bool CSMEM>
+__global__ void __launch_bounds__(kFineThreads, 1)
+    fine_list_kernel(const FineListSolve* solves, const FineListItem* items, int n_items, int* next,
+                     unsigned char* ws, size_t ws_g, size_t ws_col) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ __align__(16) FineArgs s_args;
+  unsigned char* mine = ws + (size_t)blockIdx.x * (2 * ws_g + (CSMEM ? 0 : ws_col));
+  G* b0 = reinterpret_cast<G*>(mine);
+  G* b1 = reinterpret_cast<G*>(mine + ws_g);
+  unsigned char* colbase = CSMEM ? smem + 8 * kRedSlots : mine + 2 * ws_g;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int k = s_item;
+    if (k >= n_items) break;
+    const FineListItem it = items[k];
+    const FineListSolve* S = solves + it.solve;
+    {  // the solve's arguments into shared memory (broadcast reads)
+      const int* src = reinterpret_cast<const int*>(&S->a);
+      int* dst = reinterpret_cast<int*>(&s_args);
+      for (int q = threadIdx.x; q < (int)(sizeof(FineArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    const int nx = s_args.nx;
+    const G* gin = (it.slice == 0 && S->g0) ? reinterpret_cast<const G*>(S->g0) : nullptr;
+    fine_state<G, VPT, ADAPT, CSMEM>(s_args, S->rho + (size_t)it.slice * nx, gin, b0, b1,
+                                     S->frho + (size_t)(it.slice + 1) * nx, nullptr, smem, colbase);
+    __syncthreads();  // before the next item overwrites s_args, s_item and the buffers
+  }
 }
 
 // ---------------------------------------------------------------- launch --
@@ -727,6 +839,34 @@ static cudaError_t launch_v(const FineArgs& a, size_t smem, cudaStream_t s) {
     return a.col_in_smem ? launch_t<G, VPT, true, true>(a, smem, s) : launch_t<G, VPT, true, false>(a, smem, s);
   }
   return a.col_in_smem ? launch_t<G, VPT, false, true>(a, smem, s) : launch_t<G, VPT, false, false>(a, smem, s);
+}
+
+template <class G, int VPT, bool ADAPT, bool CSMEM>
+static cudaError_t launch_list_t(const FineList& L, size_t smem, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fine_list_kernel<G, VPT, ADAPT, CSMEM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  fine_list_kernel<G, VPT, ADAPT, CSMEM><<<L.grid, kFineThreads, smem, s>>>(L.solves, L.items, L.n_items, L.next,
+                                                                            L.ws, L.ws_g, L.ws_col);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, bool col_in_smem, size_t smem,
+                             cudaStream_t s) {
+  if (fp32) {
+    if (adapt) return col_in_smem ? launch_list_t<float, 8, true, true>(L, smem, s)
+                                  : launch_list_t<float, 8, true, false>(L, smem, s);
+    return col_in_smem ? launch_list_t<float, 8, false, true>(L, smem, s)
+                       : launch_list_t<float, 8, false, false>(L, smem, s);
+  }
+  if (adapt) return col_in_smem ? launch_list_t<double, 4, true, true>(L, smem, s)
+                                : launch_list_t<double, 4, true, false>(L, smem, s);
+  return col_in_smem ? launch_list_t<double, 4, false, true>(L, smem, s)
+                     : launch_list_t<double, 4, false, false>(L, smem, s);
 }
 
 cudaError_t launch_fine(const FineArgs& args, int vpt, bool fp32, size_t smem, cudaStream_t s) {

@@ -55,7 +55,31 @@ struct FineArgs {
   // instruction is needed (or re-issued) inside the FP32 kernels' step loop
   float fa, fb, f_dx, f_inv_dx, f_inv_dv, f_kflux, f_fflux, f_inv_nx;
   float f_dx_lo, f_inv_nx_lo;  // low parts of dx and 1/nx as float-float
+  double xiM;                  // <xi M> of the discrete Maxwellian (lifting)
 };
+
+// Work list of fine propagations across solves (persistent kernel).
+struct FineListSolve {
+  FineArgs a;          // the solve's constants (shape, steps, dt, ...)
+  const double* rho;   // [N+1][nx] slice densities rho^{n,k} (input of slice n)
+  double* frho;        // [N+1][nx] F(rho^{n,k}) written at n+1
+  const void* g0;      // slice 0's perturbation (context precision) or null
+};
+struct FineListItem {
+  int solve, slice;
+};
+struct FineList {
+  const FineListSolve* solves;
+  const FineListItem* items;
+  int n_items, grid;
+  int* next;            // work counter, zero at launch
+  unsigned char* ws;    // per CTA: two step buffers of ws_g bytes (+ ws_col)
+  size_t ws_g, ws_col;
+};
+// Launch the persistent list kernel: FP32 (8 nodes per lane) or FP64 (4);
+// every solve of the list must share precision and adaptation.
+cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, bool col_in_smem, size_t smem,
+                             cudaStream_t s);
 
 // Fill the float copies of a FineArgs from its double fields.
 inline void fine_args_floats(FineArgs& a) {
@@ -118,6 +142,10 @@ struct CorrectArgs {
 cudaError_t launch_correct(const CorrectArgs& a, double* gws, cudaStream_t s);
 cudaError_t launch_coarse_chain(const MacroArgs& a, int n_slices, double* rho, double* gprev,
                                 double* gws, cudaStream_t s);
+// Many solves, one CTA each; `list` in device memory; scratch for nx_max.
+size_t macro_list_ws_bytes(int nx_max, int grid);
+cudaError_t launch_correct_list(const CorrectArgs* list, int n, int nx_max, double* gws, cudaStream_t s);
+cudaError_t launch_coarse_chain_list(const CorrectArgs* list, int n, int nx_max, double* gws, cudaStream_t s);
 
 // Everything the fine kernel needs for one call except its buffers: the
 // arguments (pointers unset), the template choice and the byte counts.
@@ -129,6 +157,15 @@ struct FinePlan {
   size_t g_bytes, rho_bytes, col_bytes, smem;
 };
 mm_status fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out);
+
+// Context access for the batch engine (mm_batch.cpp).
+const mm_params& ctx_params(const mm_ctx* c);
+int ctx_device(const mm_ctx* c);
+int64_t ctx_fine_steps(const mm_ctx* c, double span);
+MacroArgs ctx_macro_args(const mm_ctx* c, double span, double rho_bar);
+FineArgs ctx_fine_args(const mm_ctx* c, int64_t n, double dt, double rho_bar);  // pointers unset
+bool ctx_list_layout(const mm_ctx* c, int* lanes);
+double ctx_mean(const double* rho, int nx);
 
 }  // namespace mmk
 

@@ -27,7 +27,9 @@ STATUS_NAMES = ["MM_OK", "MM_ERR_INVALID", "MM_ERR_OOM", "MM_ERR_CUDA", "MM_ERR_
                 "MM_ERR_UNSTABLE", "MM_ERR_BUSY", "MM_ERR_NOT_READY", "MM_ERR_UNKNOWN_TICKET"]
 
 EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine_propagate",
-            "mm_fine_propagate_noalloc", "mm_coarse", "mm_lift", "parareal_run", "mm_server_create", "serve_submit",
+            "mm_fine_propagate_noalloc", "mm_coarse", "mm_lift", "parareal_run", "mm_batch_footprint",
+            "mm_batch_create", "mm_batch_add", "mm_batch_step", "mm_batch_query", "mm_batch_take",
+            "mm_batch_bytes", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
             "serve_poll", "mm_server_destroy", "mm_last_error"]
 
 
@@ -124,6 +126,16 @@ def load(build_if_missing: bool = True):
             "serve_poll": (ctypes.c_int, [V, ctypes.c_uint64, P(mm_result), ctypes.c_int32]),
             "mm_server_destroy": (ctypes.c_int, [V]),
             "mm_last_error": (ctypes.c_char_p, []),
+            "mm_batch_footprint": (ctypes.c_size_t, [P(mm_params), P(mm_parareal_cfg)]),
+            "mm_batch_create": (ctypes.c_int, [P(mm_alloc), P(V)]),
+            "mm_batch_add": (ctypes.c_int, [V, P(mm_params), P(mm_parareal_cfg), V, V, P(ctypes.c_uint64)]),
+            "mm_batch_step": (ctypes.c_int, [V, P(ctypes.c_int32), V]),
+            "mm_batch_query": (ctypes.c_int, [V, ctypes.c_uint64, P(ctypes.c_int32)]),
+            "mm_batch_take": (ctypes.c_int, [V, ctypes.c_uint64, V, P(mm_parareal_stats)]),
+            "mm_batch_bytes": (ctypes.c_size_t, [V]),
+            "mm_batch_destroy": (None, [V]),
+            "parareal_run_many": (ctypes.c_int, [ctypes.c_int32, P(mm_params), P(mm_parareal_cfg), P(V), P(V),
+                                                 P(V), P(mm_parareal_stats), V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -249,6 +261,89 @@ def parareal_run(ctx: Ctx, t_end: float, n_slices: int, max_iter: int, tol: floa
             "mass_drift": st.mass_drift, "fine_steps": st.fine_steps,
             "kinetic_updates": st.kinetic_updates, "elapsed_ms": st.elapsed_ms,
             "fine_ms": st.fine_ms, "fine_launches": st.fine_launches}
+
+
+def _stats_dict(st: "mm_parareal_stats") -> dict:
+    it = st.iterations
+    return {"iterations": it, "err": [st.err[k] for k in range(min(it, 64))],
+            "mass_drift": st.mass_drift, "fine_steps": st.fine_steps,
+            "kinetic_updates": st.kinetic_updates, "elapsed_ms": st.elapsed_ms,
+            "fine_ms": st.fine_ms, "fine_launches": st.fine_launches}
+
+
+class Batch:
+    """Owning handle of an mm_batch (many parareal solves advanced together)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def mm_batch_footprint(params: mm_params, t_end: float, n_slices: int, max_iter: int, tol: float) -> int:
+    cfg = mm_parareal_cfg(t_end, n_slices, max_iter, tol)
+    return load().mm_batch_footprint(ctypes.byref(params), ctypes.byref(cfg))
+
+
+def mm_batch_create() -> Batch:
+    h = ctypes.c_void_p()
+    _check(load().mm_batch_create(None, ctypes.byref(h)))
+    return Batch(h)
+
+
+def mm_batch_add(batch: Batch, params: mm_params, t_end: float, n_slices: int, max_iter: int, tol: float,
+                 rho0, g0) -> int:
+    cfg = mm_parareal_cfg(t_end, n_slices, max_iter, tol)
+    i = ctypes.c_uint64()
+    _check(load().mm_batch_add(batch.handle, ctypes.byref(params), ctypes.byref(cfg), _ptr(rho0), _ptr(g0),
+                               ctypes.byref(i)))
+    return i.value
+
+
+def mm_batch_step(batch: Batch, stream=None) -> int:
+    a = ctypes.c_int32()
+    _check(load().mm_batch_step(batch.handle, ctypes.byref(a), _stream(stream)))
+    return a.value
+
+
+def mm_batch_query(batch: Batch, solve_id: int) -> bool:
+    d = ctypes.c_int32()
+    _check(load().mm_batch_query(batch.handle, solve_id, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def mm_batch_take(batch: Batch, solve_id: int, rho_slices_out) -> dict:
+    st = mm_parareal_stats()
+    _check(load().mm_batch_take(batch.handle, solve_id, _ptr(rho_slices_out), ctypes.byref(st)))
+    return _stats_dict(st)
+
+
+def mm_batch_bytes(batch: Batch) -> int:
+    return load().mm_batch_bytes(batch.handle)
+
+
+def mm_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def parareal_run_many(params: list, cfgs: list, rho0: list, g0: list, outs: list, stream=None) -> list:
+    """cfgs: (t_end, n_slices, max_iter, tol) tuples; arrays host or device."""
+    n = len(params)
+    P = (mm_params * n)(*params)
+    C = (mm_parareal_cfg * n)(*[mm_parareal_cfg(*c) for c in cfgs])
+    V = ctypes.c_void_p
+    R = (V * n)(*[_ptr(a) for a in rho0])
+    G = (V * n)(*[_ptr(a) for a in g0])
+    O = (V * n)(*[_ptr(a) for a in outs])
+    S = (mm_parareal_stats * n)()
+    _check(load().parareal_run_many(n, P, C, R, G, O, S, _stream(stream)))
+    return [_stats_dict(S[q]) for q in range(n)]
 
 
 class Server:
