@@ -349,18 +349,27 @@ typedef struct {
   int64_t kinetic_updates;
 } mm_result;
 
-/* Serving loop with continuous batching: requests are admitted while their
-   device footprint fits the budget and a slot is free; the fine
-   propagations of all resident solves share launches.
+/* Serving loop with continuous batching.  One scheduler thread owns an
+   mm_batch and a stream and runs rounds: it admits queued requests (first
+   come, first served) while their device footprint fits hbm_budget_bytes
+   and fewer than max_slots solves are resident, runs one parareal
+   iteration of every resident solve (all their fine propagations in one
+   persistent work-list launch), and completes the solves that finished.
+   A request's footprint is mm_batch_footprint plus its share of the fine
+   kernel's step buffers (two states per SM) plus 1 MiB.  Requests that
+   arrive while others run join at the next round; a result does not depend
+   on the requests it ran with.  If a round fails, the solves resident in
+   it fail with its status and the server continues with the queue.
    Errors: MM_ERR_INVALID, MM_ERR_CUDA, MM_ERR_OOM. */
 MM_API mm_status mm_server_create(const mm_server_cfg* cfg, const mm_alloc* alloc,
                            mm_server** out);
 /* Copy the request and queue it.  Errors: MM_ERR_INVALID (bad request, or
    a footprint above the whole budget). */
 MM_API mm_status serve_submit(mm_server* s, const mm_request* req, uint64_t* ticket);
-/* Wait up to timeout_ms for a result; on MM_OK the result is copied into
-   *res and the ticket is retired.  Errors: MM_ERR_NOT_READY,
-   MM_ERR_UNKNOWN_TICKET. */
+/* Wait up to timeout_ms (at most the server's wait_limit_ms) for a result;
+   on MM_OK the result (its own status, the density at t_end, iterations,
+   latency from submit to completion) is copied into *res and the ticket is
+   retired.  Errors: MM_ERR_NOT_READY, MM_ERR_UNKNOWN_TICKET. */
 MM_API mm_status serve_poll(mm_server* s, uint64_t ticket, mm_result* res,
                      int32_t timeout_ms);
 /* Stop the scheduler, fail queued requests, free device state. */

@@ -1,12 +1,14 @@
-// Serving loop of the C ABI (serve_submit / serve_poll).
+// Serving loop of the C ABI (serve_submit / serve_poll) with continuous
+// batching.
 //
 // Requests carry a full problem (parameters, parareal configuration, host
-// initial data).  A scheduler thread admits queued requests while their
-// device footprint fits the HBM budget and a slot is free, and runs each
-// admitted solve with parareal_run on its own stream from a small pool of
-// worker threads, so solves that arrive while others are on the GPU overlap
-// on the device.  Results are copied to host memory owned by the server
-// until polled.
+// initial data).  One scheduler thread owns a batch (mm_batch.cpp) and a
+// stream, and runs rounds: it admits queued requests while their device
+// footprint fits the HBM budget and a slot is free, runs one parareal
+// iteration of every resident solve (the fine propagations of all of them
+// share one persistent work-list launch), and hands out the solves that
+// finished.  A request that arrives while others are on the GPU joins at the
+// next round; its result does not depend on which other solves it ran with.
 #include <math.h>
 #include <string.h>
 
@@ -33,6 +35,7 @@ struct Job {
   std::vector<unsigned char> g0;
   size_t footprint = 0;
   Clock::time_point t_submit;
+  uint64_t batch_id = 0;
   // result
   bool done = false;
   mm_status status = MM_OK;
@@ -42,15 +45,6 @@ struct Job {
   int64_t kinetic_updates = 0;
 };
 
-size_t footprint_of(const mm_params& p, const mm_parareal_cfg& c) {
-  const size_t gsz = p.precision == MM_FP32G ? 4 : 8;
-  const size_t N = c.n_slices;
-  // slices (3 arrays of N+1 densities), fine inputs and double buffer,
-  // fine column arrays, staging
-  return 3 * (N + 1) * p.nx * 8 + 3 * N * (size_t)p.nx * p.nv * gsz + N * (size_t)p.nx * 512 +
-         (size_t)p.nx * p.nv * gsz + (1u << 20);
-}
-
 }  // namespace
 
 struct mm_server {
@@ -58,59 +52,97 @@ struct mm_server {
   mm_alloc alloc{};
   bool has_alloc = false;
   int device = 0;
+  int n_sm = 1;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<std::shared_ptr<Job>> queue;
-  std::map<uint64_t, std::shared_ptr<Job>> jobs;
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;  // by ticket, until polled
   size_t in_use = 0;
   int running = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread sched;
-  std::vector<std::thread> workers;
 
-  void run_job(std::shared_ptr<Job> j) {
-    cudaSetDevice(device);
-    cudaStream_t s;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    mm_ctx* ctx = nullptr;
-    mm_status st = mm_create(&j->params, has_alloc ? &alloc : nullptr, &ctx);
-    std::vector<double> slices((size_t)(j->cfg.n_slices + 1) * j->params.nx);
-    mm_parareal_stats ps{};
-    if (st == MM_OK) st = parareal_run(ctx, &j->cfg, j->rho0.data(), j->g0.data(), slices.data(), &ps, s);
-    if (ctx) mm_destroy(ctx);
-    cudaStreamDestroy(s);
+  // device bytes a request holds while resident: its arrays plus its share
+  // of the fine kernel's per-CTA step buffers (sized for the largest state)
+  size_t footprint_of(const mm_params& p, const mm_parareal_cfg& c) const {
+    const size_t gsz = p.precision == MM_FP32G ? 4 : 8;
+    return mm_batch_footprint(&p, &c) + 2 * (size_t)p.nx * p.nv * gsz * n_sm + (1u << 20);
+  }
+
+  void finish(const std::shared_ptr<Job>& j, mm_status st) {
     std::lock_guard<std::mutex> lk(mu);
     j->status = st;
-    j->iterations = ps.iterations;
-    j->kinetic_updates = ps.kinetic_updates;
-    if (st == MM_OK)
-      j->rho_T.assign(slices.end() - j->params.nx, slices.end());
     j->latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - j->t_submit).count();
     j->done = true;
     in_use -= j->footprint;
     --running;
     cv_done.notify_all();
-    cv_sched.notify_all();
   }
 
   void scheduler() {
-    std::unique_lock<std::mutex> lk(mu);
+    cudaSetDevice(device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    mm_batch* batch = nullptr;
+    mm_status bst = mm_batch_create(has_alloc ? &alloc : nullptr, &batch);
+    std::map<uint64_t, std::shared_ptr<Job>> inflight;  // by batch id
     while (true) {
-      cv_sched.wait(lk, [&] {
-        if (stop) return true;
-        if (queue.empty()) return false;
-        auto& j = queue.front();
-        return running < cfg.max_slots && in_use + j->footprint <= cfg.hbm_budget_bytes;
-      });
-      if (stop) break;
-      auto j = queue.front();
-      queue.pop_front();
-      in_use += j->footprint;
-      ++running;
-      // reap finished threads, then start this job
-      workers.emplace_back([this, j] { run_job(j); });
+      std::vector<std::shared_ptr<Job>> admit;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_sched.wait(lk, [&] { return stop || !queue.empty() || !inflight.empty(); });
+        if (stop) break;
+        while (!queue.empty() && running < cfg.max_slots &&
+               in_use + queue.front()->footprint <= cfg.hbm_budget_bytes) {
+          admit.push_back(queue.front());
+          in_use += queue.front()->footprint;
+          ++running;
+          queue.pop_front();
+        }
+      }
+      for (auto& j : admit) {
+        if (bst != MM_OK) {
+          finish(j, bst);
+          continue;
+        }
+        mm_status st = mm_batch_add(batch, &j->params, &j->cfg, j->rho0.data(), j->g0.data(), &j->batch_id);
+        if (st != MM_OK) finish(j, st);
+        else inflight[j->batch_id] = j;
+      }
+      if (inflight.empty()) continue;
+      int32_t active = 0;
+      mm_status st = mm_batch_step(batch, &active, s);
+      if (st != MM_OK) {  // the round failed: every resident solve fails with it
+        for (auto& kv : inflight) finish(kv.second, st);
+        inflight.clear();
+        mm_batch_destroy(batch);
+        bst = mm_batch_create(has_alloc ? &alloc : nullptr, &batch);
+        continue;
+      }
+      for (auto it = inflight.begin(); it != inflight.end();) {
+        int32_t done = 0;
+        mm_batch_query(batch, it->first, &done);
+        if (!done) {
+          ++it;
+          continue;
+        }
+        auto j = it->second;
+        std::vector<double> slices((size_t)(j->cfg.n_slices + 1) * j->params.nx);
+        mm_parareal_stats ps{};
+        const mm_status ts = mm_batch_take(batch, it->first, slices.data(), &ps);
+        if (ts == MM_OK) {
+          j->rho_T.assign(slices.end() - j->params.nx, slices.end());
+          j->iterations = ps.iterations;
+          j->kinetic_updates = ps.kinetic_updates;
+        }
+        finish(j, ts);
+        it = inflight.erase(it);
+      }
     }
+    for (auto& kv : inflight) finish(kv.second, MM_ERR_INVALID);
+    if (batch) mm_batch_destroy(batch);
+    cudaStreamDestroy(s);
   }
 };
 
@@ -126,6 +158,8 @@ extern "C" mm_status mm_server_create(const mm_server_cfg* cfg, const mm_alloc* 
     s->has_alloc = true;
   }
   cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
+  if (s->n_sm <= 0) s->n_sm = 1;
   s->sched = std::thread([s] { s->scheduler(); });
   *out = s;
   return MM_OK;
@@ -143,11 +177,12 @@ extern "C" mm_status serve_submit(mm_server* s, const mm_request* req, uint64_t*
   const size_t gb = (size_t)p.nx * p.nv * (p.precision == MM_FP32G ? 4 : 8);
   j->g0.resize(gb);
   memcpy(j->g0.data(), req->g0, gb);
-  j->footprint = footprint_of(p, req->cfg);
+  j->footprint = s->footprint_of(p, req->cfg);
   if (j->footprint > s->cfg.hbm_budget_bytes)
     return mm_fail(MM_ERR_INVALID, "request footprint exceeds the whole HBM budget");
   j->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return mm_fail(MM_ERR_INVALID, "server is stopping");
   j->ticket = s->next_ticket++;
   s->jobs[j->ticket] = j;
   s->queue.push_back(j);
@@ -162,7 +197,8 @@ extern "C" mm_status serve_poll(mm_server* s, uint64_t ticket, mm_result* res, i
   auto it = s->jobs.find(ticket);
   if (it == s->jobs.end()) return mm_fail(MM_ERR_UNKNOWN_TICKET, "unknown ticket");
   auto j = it->second;
-  if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(0, (int)timeout_ms)), [&] { return j->done; }))
+  const int wait = std::min(std::max(0, (int)timeout_ms), s->cfg.wait_limit_ms);
+  if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(wait), [&] { return j->done; }))
     return mm_fail(MM_ERR_NOT_READY, "result not ready");
   res->status = j->status;
   res->iterations = j->iterations;
@@ -186,8 +222,6 @@ extern "C" mm_status mm_server_destroy(mm_server* s) {
   }
   s->cv_sched.notify_all();
   if (s->sched.joinable()) s->sched.join();
-  for (auto& t : s->workers)
-    if (t.joinable()) t.join();
   s->cv_done.notify_all();
   delete s;
   return MM_OK;

@@ -1,0 +1,85 @@
+"""Serving with continuous batching (mm_server_create / serve_submit /
+serve_poll): every result equals the same solve run alone, whatever it was
+batched with; admission respects the HBM budget; failures are reported per
+request."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2511_13386_gb300 import mm
+from tests.gpu_helpers import device
+from tests.test_gpu_batch import _host_g0, _mixed_set, _run_batch
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _footprint(p, t_end, N, K):
+    gsz = 4 if p.precision == mm.MM_FP32G else 8
+    n_sm = torch.cuda.get_device_properties(device()).multi_processor_count
+    return mm.mm_batch_footprint(p, t_end, N, K, 0.0) + 2 * p.nx * p.nv * gsz * n_sm + (1 << 20)
+
+
+def _serve(solves, budget, slots, stagger_s=0.0):
+    srv = mm.mm_server_create(budget, slots, wait_limit_ms=60000)
+    tickets = []
+    for (p, w, t_end, N, K) in solves:
+        tickets.append(mm.serve_submit(srv, p, t_end, N, K, 0.0, np.ascontiguousarray(w.rho0), _host_g0(p, w)))
+        if stagger_s:
+            time.sleep(stagger_s)
+    res = []
+    for t, (p, w, *_r) in zip(tickets, solves):
+        r = mm.serve_poll(srv, t, w.nx, timeout_ms=60000)
+        assert r is not None
+        res.append(r)
+    srv.close()
+    return res
+
+
+def test_serving_results_equal_solo_runs():
+    solves = _mixed_set()
+    solo = [_run_batch([s])[0][0][-1] for s in solves]
+    for stagger in (0.0, 0.002):
+        res = _serve(solves, budget=1 << 40, slots=64, stagger_s=stagger)
+        for q, r in enumerate(res):
+            assert r["status"] == mm.MM_OK
+            assert r["iterations"] == solves[q][4]
+            assert r["latency_ns"] > 0
+            assert np.array_equal(r["rho_T"], solo[q]), q
+
+
+def test_serving_budget_serialises_admission():
+    solves = _mixed_set()[:4]
+    biggest = max(_footprint(p, t, N, K) for (p, w, t, N, K) in solves)
+    res = _serve(solves, budget=biggest, slots=64)  # one resident solve at a time
+    solo = [_run_batch([s])[0][0][-1] for s in solves]
+    for q, r in enumerate(res):
+        assert r["status"] == mm.MM_OK
+        assert np.array_equal(r["rho_T"], solo[q])
+    res1 = _serve(solves, budget=1 << 40, slots=1)  # one slot
+    for q, r in enumerate(res1):
+        assert np.array_equal(r["rho_T"], solo[q])
+
+
+def test_serving_rejections_and_per_request_failures():
+    (p, w, t_end, N, K) = _mixed_set()[0]
+    srv = mm.mm_server_create(_footprint(p, t_end, N, K) - 1, 4)
+    with pytest.raises(mm.MMError) as e:  # above the whole budget
+        mm.serve_submit(srv, p, t_end, N, K, 0.0, np.ascontiguousarray(w.rho0), _host_g0(p, w))
+    assert e.value.status == mm.MM_ERR_INVALID
+    with pytest.raises(mm.MMError) as e:
+        mm.serve_poll(srv, 999, w.nx)
+    assert e.value.status == mm.MM_ERR_UNKNOWN_TICKET
+    srv.close()
+    # a request the batch refuses (no 8-node lanes) fails alone; the other completes
+    srv = mm.mm_server_create(1 << 40, 4)
+    bad = mm.mm_params_default(nx=64, nv=20, eps=1.0, precision=mm.MM_FP32G, rho_bar=1.0)
+    tb = mm.serve_submit(srv, bad, 0.01, 2, 1, 0.0, np.ones(64), np.zeros((64, 20), np.float32))
+    tg = mm.serve_submit(srv, p, t_end, N, K, 0.0, np.ascontiguousarray(w.rho0), _host_g0(p, w))
+    rb = mm.serve_poll(srv, tb, 64, timeout_ms=60000)
+    rg = mm.serve_poll(srv, tg, w.nx, timeout_ms=60000)
+    srv.close()
+    assert rb["status"] == mm.MM_ERR_INVALID
+    assert rg["status"] == mm.MM_OK
+    assert np.array_equal(rg["rho_T"], _run_batch([(p, w, t_end, N, K)])[0][0][-1])
