@@ -50,7 +50,14 @@ def parse():
     ap.add_argument("--kernel-only", default=None, choices=["fine", "coarse"],
                     help="profiling driver: launch only this kernel on the workload")
     ap.add_argument("--window", type=int, default=200,
-                    help="fine steps per launch in --kernel-only fine")
+                    help="fine steps per launch in --kernel-only fine; fine steps per slice in the "
+                         "many-solve and serving workloads")
+    ap.add_argument("--workload", default="batched", choices=["batched", "many", "serving"],
+                    help="batched (default, the headline line); many: 2048 independent solves of random "
+                         "sizes in one batch; serving: open-loop Poisson arrivals through the server")
+    ap.add_argument("--solves", type=int, default=2048, help="solves of the many-solve workload")
+    ap.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals (serving)")
+    ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second (serving)")
     return ap.parse_args()
 
 
@@ -315,10 +322,174 @@ def run_ours(a, rank, world, dist):
             "clocks": clk.summary(), "n_steps_fine": q["n_steps"], "fine_launches": fine_n}
 
 
+# ----------------------------------------------------- many-solve workload --
+
+def _window_t_end(mm, p, n_slices, window):
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    return n_slices * window * dt * (1 - 1e-9)
+
+
+def run_many(a):
+    """Many-solve batching: `--solves` independent parareal solves drawn as
+    in the many-solve workload (Nx in 128..8192, Nv in 32..256, eps
+    log-uniform in [1e-4, 1], N in 16..256 slices, adaptation on, FP32 g),
+    each on a fixed window of `--window` fine steps per slice (T=1 would need
+    up to 1e9 steps per slice).  One step = one parareal iteration of every
+    solve through mm_batch_step (coarse guess on the first, every fine
+    propagation of every solve in one persistent work-list launch, the
+    corrections); value = kinetic cell-updates per second over the timed
+    steps."""
+    import numpy as np
+    import torch
+
+    from paper_2511_13386_gb300 import mm, workloads as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    solves = W.many(a.solves, lazy=True)
+    b = mm.mm_batch_create()
+    K = a.warmup + a.steps
+    t0 = time.perf_counter()
+    for w in solves:
+        w = W.materialise(w)
+        p = mm.mm_params_default(nx=w.nx, nv=w.nv, eps=w.eps, v_max=w.v_max, rho_bar=1.0, adapt=1,
+                                 thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, precision=mm.MM_FP32G)
+        t_end = _window_t_end(mm, p, w.n_slices, a.window)
+        mm.mm_batch_add(b, p, t_end, w.n_slices, K, 0.0, np.ascontiguousarray(w.rho0),
+                        np.ascontiguousarray(w.g0.astype(np.float32)))
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        mm.mm_batch_step(b)
+    c0 = mm.mm_batch_counters(b)
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(a.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mm.mm_batch_step(b, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    c1 = mm.mm_batch_counters(b)
+    upd = c1["kinetic_updates"] - c0["kinetic_updates"]
+    total_ms = sum(ms)
+    mem = mm.mm_batch_bytes(b)
+    b.close()
+    items = sum(w.n_slices for w in solves)
+    line = {"metric": "cell-updates/s", "value": upd / (total_ms / 1e3), "unit": "cell-updates/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"many-solve batching: {len(solves)} solves, Nx 128..8192, Nv 32..256, "
+                                   f"eps 1e-4..1, N 16..256, adaptation on, {a.window} fine steps per slice; "
+                                   f"one parareal iteration of every solve per step",
+                       "fine_items_first_iteration": items, "resident_bytes": mem,
+                       "fine_launch_ms": (c1["fine_ms"] - c0["fine_ms"]) / a.steps,
+                       "setup_s": round(setup_s, 1)},
+            "gpu_launches": 3 * a.steps, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
+# -------------------------------------------------------- serving workload --
+
+def run_serving(a):
+    """Serving: open-loop Poisson arrivals (`--rate` per second for
+    `--duration` s) of solves drawn as in the many-solve workload plus 5%
+    large solves (Nx=32768, Nv=256, N=512), each a parareal solve with K=2
+    on a window of `--window` fine steps per slice, FP32 g, through the
+    server (continuous batching, 150 GB admission budget).  Reports p50/p99
+    latency (submit -> result) and aggregate cell-updates/s, and beside it
+    the plain per-solve FP64 GPU path (parareal_run, FP64) on a sample of the
+    same requests run alone."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2511_13386_gb300 import mm, workloads as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    arrivals = W.serving(rate=a.rate, duration=a.duration)
+    reqs = []
+    for ar in arrivals:  # initial data built before the clock starts (FP32 g only)
+        w = W.materialise(ar.workload)
+        p = mm.mm_params_default(nx=w.nx, nv=w.nv, eps=w.eps, v_max=w.v_max, rho_bar=1.0, adapt=1,
+                                 thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, precision=mm.MM_FP32G)
+        g32 = np.ascontiguousarray(w.g0.astype(np.float32))
+        reqs.append((ar.t, ar.workload, p, _window_t_end(mm, p, w.n_slices, a.window),
+                     np.ascontiguousarray(w.rho0), g32))
+    K = 2
+    srv = mm.mm_server_create(150 * 10 ** 9, 100000, wait_limit_ms=600000)
+    tickets = [None] * len(reqs)
+    results = [None] * len(reqs)
+
+    def poller():
+        for q in range(len(reqs)):
+            while tickets[q] is None:
+                time.sleep(0.0005)
+            results[q] = mm.serve_poll(srv, tickets[q], reqs[q][1].nx, timeout_ms=600000)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        for q, (t, w, p, t_end, r0, g0) in enumerate(reqs):
+            delay = t - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[q] = mm.serve_submit(srv, p, t_end, w.n_slices, K, 0.0, r0, g0)
+        th.join()
+        wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r["latency_ns"] for r in results]) / 1e6
+    ok = sum(r["status"] == mm.MM_OK for r in results)
+    upd = sum(r["kinetic_updates"] for r in results)
+    # plain per-solve FP64 path on a sample (each alone, device arrays)
+    # (the FP64 streaming kernel holds at most 32 lanes of 4 nodes: nv <= 128)
+    sample = [q for q in range(0, len(reqs), max(1, len(reqs) // 24)) if reqs[q][1].nv <= 128]
+    f_upd, f_ms = 0, 0.0
+    for q in sample:
+        t, w, p, t_end, r0, g0 = reqs[q]
+        w = W.materialise(w)
+        p64 = mm.mm_params_default(nx=w.nx, nv=w.nv, eps=w.eps, v_max=w.v_max, rho_bar=1.0, adapt=1,
+                                   thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, precision=mm.MM_FP64)
+        ctx = mm.mm_create(p64)
+        out = torch.empty((w.n_slices + 1, w.nx), dtype=torch.float64, device=dev)
+        info = mm.parareal_run(ctx, t_end, w.n_slices, K, 0.0, torch.tensor(w.rho0, device=dev),
+                               torch.tensor(w.g0, device=dev), out)
+        ctx.close()
+        f_upd += info["kinetic_updates"]
+        f_ms += info["elapsed_ms"]
+    line = {"metric": "cell-updates/s", "value": upd / wall, "unit": "cell-updates/s", "n_gpus": 1,
+            "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / max(len(reqs), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving: Poisson arrivals {a.rate}/s for {a.duration} s, many-solve "
+                                   f"sizes + 5% Nx=32768 Nv=256 N=512, K={K}, {a.window} fine steps per "
+                                   f"slice, 150 GB budget, continuous batching",
+                       "requests": len(reqs), "completed_ok": ok,
+                       "large_requests": sum(1 for r in reqs if r[1].nx == 32768)},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "fp64_per_solve": {"value": f_upd / (f_ms / 1e3), "unit": "cell-updates/s",
+                               "sample_requests": len(sample),
+                               "path": "parareal_run, FP64, each request alone (requests with nv <= 128)"},
+            "wall_s": wall, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     if a.kernel_only:
         kernel_only(a)
+        return
+    if a.workload == "many" and a.impl == "ours":
+        run_many(a)
+        return
+    if a.workload == "serving" and a.impl == "ours":
+        run_serving(a)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -314,6 +314,10 @@ MM_API mm_status mm_batch_query(mm_batch* b, uint64_t id, int32_t* done);
 MM_API mm_status mm_batch_take(mm_batch* b, uint64_t id, double* rho_slices_out,
                         mm_parareal_stats* stats);
 MM_API size_t mm_batch_bytes(const mm_batch* b);
+/* Totals over the batch's life: kinetic cell-updates of all fine
+   propagations, fine launches, and their device time (events). */
+MM_API mm_status mm_batch_counters(const mm_batch* b, int64_t* kinetic_updates, int32_t* fine_launches,
+                            double* fine_ms);
 MM_API void mm_batch_destroy(mm_batch* b);
 
 /* parareal_run for n solves at once through a batch: rho0[q], g0[q],

@@ -222,17 +222,28 @@ void orc_update_status(const orc_params* p, const double* rho,
 /* ------------------------------------------------------------ dt rule --- */
 
 /* Reading (the paper states no time-step rule): theta times the largest s
-   such that
-   (i)   eps (1 - e^{-s/eps^2}) v_max / dx <= (1 + e^{-s/eps^2}) / 2,
-   (ii)  s (1 - e^{-s/eps^2}) <= dx^2 / (2 m2),
-   (iii) adaptation on: s <= dx^2 / (2 m2),
+   such that, with a = e^{-s/eps^2},
+     phi_t = 2 eps (1 - a) v_max / (dx (1 + a))   (upwind transport of g
+                                                    with relaxation),
+     phi_d = 2 m2 s (1 - a) / dx^2                 (diffusion of rho
+                                                    through g),
+   (i)   phi_t <= 1,
+   (ii)  phi_d <= 1,
+   (iv)  phi_d + phi_t / 4 <= 1 (the two couple: the linearised step's
+         spectral radius exceeds one near the limit of (ii) once phi_t is
+         large; the critical phi_d measured by a von Neumann analysis is
+         about 1 - 0.21 phi_t in the diffusive regime),
+   (iii) adaptation on: 2 m2 s / dx^2 <= 1 (explicit S^0 in fluid cells),
    the largest s found by bisection. */
 static int dt_ok(const orc_params* p, double m2, double s) {
   const double dx = dx_of(p);
   const double a = exp(-s / (p->eps * p->eps));
-  if (p->eps * (1.0 - a) * p->v_max / dx > 0.5 * (1.0 + a)) return 0;
-  if (s * (1.0 - a) > dx * dx / (2.0 * m2)) return 0;
-  if (p->adapt && s > dx * dx / (2.0 * m2)) return 0;
+  const double phi_t = 2.0 * p->eps * (1.0 - a) * p->v_max / (dx * (1.0 + a));
+  const double phi_d = 2.0 * m2 * s * (1.0 - a) / (dx * dx);
+  if (phi_t > 1.0) return 0;
+  if (phi_d > 1.0) return 0;
+  if (phi_d + 0.25 * phi_t > 1.0) return 0;
+  if (p->adapt && 2.0 * m2 * s / (dx * dx) > 1.0) return 0;
   return 1;
 }
 

@@ -150,18 +150,21 @@ static mmk::VelocityGrid build_velocity_grid(int nv, double v_max) {
 }
 
 // Stability rule for the step (the paper states none).  With
-// a(s) = exp(-s/eps^2) the step s must satisfy
-//   upwind transport with relaxation: eps (1-a) v_max / dx <= (1+a)/2,
-//   diffusion through g:              s (1-a) <= dx^2 / (2 m2),
-//   explicit S^0 in fluid cells:      s <= dx^2 / (2 m2)   (adaptation on);
-// the largest such s is bracketed and bisected.
+// a(s) = exp(-s/eps^2), phi_t = 2 eps (1-a) v_max / (dx (1+a)) (upwind
+// transport of g with relaxation) and phi_d = 2 m2 s (1-a) / dx^2
+// (diffusion of rho through g), the step s must satisfy phi_t <= 1,
+// phi_d <= 1, phi_d + phi_t / 4 <= 1 (the two couple: a von Neumann
+// analysis of the linearised step puts the critical phi_d near
+// 1 - 0.21 phi_t in the diffusive regime) and, with adaptation, the explicit
+// S^0 limit 2 m2 s / dx^2 <= 1 in fluid cells; the largest such s is
+// bracketed and bisected.
 static bool step_ok(const mm_params& p, double m2, double s) {
   const double dx = p.x_len / p.nx;
   const double a = exp(-s / (p.eps * p.eps));
-  const double lim = dx * dx / (2.0 * m2);
-  if (p.eps * (1.0 - a) * p.v_max / dx > 0.5 * (1.0 + a)) return false;
-  if (s * (1.0 - a) > lim) return false;
-  if (p.adapt && s > lim) return false;
+  const double phi_t = 2.0 * p.eps * (1.0 - a) * p.v_max / (dx * (1.0 + a));
+  const double phi_d = 2.0 * m2 * s * (1.0 - a) / (dx * dx);
+  if (phi_t > 1.0 || phi_d > 1.0 || phi_d + 0.25 * phi_t > 1.0) return false;
+  if (p.adapt && 2.0 * m2 * s / (dx * dx) > 1.0) return false;
   return true;
 }
 

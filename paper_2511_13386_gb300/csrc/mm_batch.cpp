@@ -58,6 +58,7 @@ struct mm_batch {
   Buf fine_ws, macro_ws, tables, items, corr, counters;
   double fine_ms = 0;
   int fine_launches = 0;
+  int64_t kin_total = 0;
 
   void* dalloc(size_t bytes, cudaStream_t s) {
     void* p = nullptr;
@@ -330,6 +331,7 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
     Solve* v = act[q];
     v->errs.push_back(errs[q]);
     v->kin += (int64_t)kin[q];
+    b->kin_total += (int64_t)kin[q];
     ++v->k;
     if (v->k >= v->K || errs[q] < v->cfg.tol) v->done = true;
   }
@@ -396,6 +398,15 @@ extern "C" void mm_batch_destroy(mm_batch* b) {
 }
 
 extern "C" size_t mm_batch_bytes(const mm_batch* b) { return b ? b->bytes_in_use : 0; }
+
+extern "C" mm_status mm_batch_counters(const mm_batch* b, int64_t* kinetic_updates, int32_t* fine_launches,
+                                       double* fine_ms) {
+  if (!b) return mm_fail(MM_ERR_INVALID, "batch is NULL");
+  if (kinetic_updates) *kinetic_updates = b->kin_total;
+  if (fine_launches) *fine_launches = b->fine_launches;
+  if (fine_ms) *fine_ms = b->fine_ms;
+  return MM_OK;
+}
 
 extern "C" mm_status parareal_run_many(int32_t n, const mm_params* params, const mm_parareal_cfg* cfgs,
                                        const double* const* rho0, const void* const* g0,

@@ -29,7 +29,7 @@ STATUS_NAMES = ["MM_OK", "MM_ERR_INVALID", "MM_ERR_OOM", "MM_ERR_CUDA", "MM_ERR_
 EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine_propagate",
             "mm_fine_propagate_noalloc", "mm_coarse", "mm_lift", "parareal_run", "mm_batch_footprint",
             "mm_batch_create", "mm_batch_add", "mm_batch_step", "mm_batch_query", "mm_batch_take",
-            "mm_batch_bytes", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
+            "mm_batch_bytes", "mm_batch_counters", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
             "serve_poll", "mm_server_destroy", "mm_last_error"]
 
 
@@ -133,6 +133,7 @@ def load(build_if_missing: bool = True):
             "mm_batch_query": (ctypes.c_int, [V, ctypes.c_uint64, P(ctypes.c_int32)]),
             "mm_batch_take": (ctypes.c_int, [V, ctypes.c_uint64, V, P(mm_parareal_stats)]),
             "mm_batch_bytes": (ctypes.c_size_t, [V]),
+            "mm_batch_counters": (ctypes.c_int, [V, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_double)]),
             "mm_batch_destroy": (None, [V]),
             "parareal_run_many": (ctypes.c_int, [ctypes.c_int32, P(mm_params), P(mm_parareal_cfg), P(V), P(V),
                                                  P(V), P(mm_parareal_stats), V]),
@@ -326,6 +327,12 @@ def mm_batch_take(batch: Batch, solve_id: int, rho_slices_out) -> dict:
 
 def mm_batch_bytes(batch: Batch) -> int:
     return load().mm_batch_bytes(batch.handle)
+
+
+def mm_batch_counters(batch: Batch) -> dict:
+    k, n, t = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().mm_batch_counters(batch.handle, ctypes.byref(k), ctypes.byref(n), ctypes.byref(t)))
+    return {"kinetic_updates": k.value, "fine_launches": n.value, "fine_ms": t.value}
 
 
 def mm_batch_destroy(batch: Batch):

@@ -191,10 +191,12 @@ POW2_NX = (128, 256, 512, 1024, 2048, 4096, 8192)
 NV_CHOICES = (32, 64, 128, 256)
 
 
-def many(n_solves: int = 2048, seed: int = SEED_BASE) -> list[Workload]:
+def many(n_solves: int = 2048, seed: int = SEED_BASE, lazy: bool = False) -> list[Workload]:
     """Many-solve batching: independent solves of random sizes (Nx a power of
     two in 128..8192, Nv in {32,64,128,256}, eps log-uniform in [1e-4, 1],
-    N uniform in 16..256), data as 'batched', adaptation on."""
+    N uniform in 16..256), data as 'batched', adaptation on.  With
+    lazy=True the initial data is left empty (sizes only); materialise()
+    fills it in."""
     rng = SplitMix64(seed)
     out = []
     for s in range(n_solves):
@@ -202,9 +204,9 @@ def many(n_solves: int = 2048, seed: int = SEED_BASE) -> list[Workload]:
         nv = NV_CHOICES[int(rng.uniform() * len(NV_CHOICES))]
         eps = 10.0 ** (-4.0 * rng.uniform())
         n = 16 + int(rng.uniform() * 241)
-        w = batched(nx, nv, eps, seed=seed + s, n_slices=n)
-        out.append(replace(w, name="many", adapt=True, thr_g=1e-3, thr_R=1e-2,
-                           r_scale=1, max_iter=8))
+        w = Workload("many", nx, nv, eps=eps, n_slices=n, max_iter=8, adapt=True, thr_g=1e-3,
+                     thr_R=1e-2, r_scale=1, seed=seed + s)
+        out.append(w if lazy else materialise(w))
     return out
 
 
