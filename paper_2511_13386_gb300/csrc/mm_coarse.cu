@@ -6,9 +6,12 @@
 //
 // One CTA of 256 threads owns one density; the linearly implicit step
 // solves the cyclic tridiagonal system (I - m2 dt L_E) rho^{m+1} = rho^m
-// with E frozen from rho^m by Sherman-Morrison on top of a Thomas sweep
-// run by one thread (the system is strictly diagonally dominant for the
-// slice lengths used, so no pivoting is needed).
+// with E frozen from rho^m by a partitioned solve: Thomas sweeps over
+// chunks of about 8 rows in parallel, parallel cyclic reduction on the
+// chunk separators (the system is strictly diagonally dominant for the
+// slice lengths used, so no pivoting is needed).  FP64 latency on GB300
+// (~70 cycles per dependent add or FMA, ~600 per division) makes the length
+// of the serial chains, not the operation count, the cost.
 #include <math.h>
 
 #include "mm_internal.h"
@@ -71,34 +74,43 @@ __device__ void limit_step_block(double* rho, double* E, double* J, const MacroA
   __syncthreads();
 }
 
-// Cyclic tridiagonal solve of a small system by Thomas + Sherman-Morrison
-// (one thread): lo[p] x[p-1] + di[p] x[p] + up[p] x[p+1] = d[p], periodic,
-// n >= 3.  x may alias d; z is scratch of n doubles.
-__device__ void cyclic_small(int n, const double* lo, const double* di, const double* up,
-                             const double* d, double* x, double* cw, double* z) {
-  const double alpha = up[n - 1], beta = lo[0], gamma = -di[0];
-  double bet = di[0] - gamma;
-  double inv = 1.0 / bet;
-  double xr = d[0] * inv, xu = gamma * inv;
-  x[0] = xr;
-  z[0] = xu;
-  for (int i = 1; i < n; ++i) {
-    const double dii = (i == n - 1) ? di[n - 1] - alpha * beta / gamma : di[i];
-    const double ci = up[i - 1] * inv;
-    cw[i] = ci;
-    bet = dii - lo[i] * ci;
-    inv = 1.0 / bet;
-    xr = (d[i] - lo[i] * xr) * inv;
-    xu = ((i == n - 1 ? alpha : 0.0) - lo[i] * xu) * inv;
-    x[i] = xr;
-    z[i] = xu;
+// Cyclic tridiagonal system of P rows (P a power of two, <= blockDim.x),
+// row i: A_i x_{i-1} + B_i x_i + C_i x_{i+1} = D_i (indices mod P), by
+// parallel cyclic reduction: at stride s every row eliminates its
+// neighbours at distance s, so after log2(P) levels row i couples x_i only
+// with x_{i +- P} = x_i itself.  One reciprocal per row and level (FP64
+// divisions are ~600 cycles on this GPU; the chain is log2(P) levels deep
+// instead of P rows).  A, B, C, D are overwritten; x receives the solution.
+__device__ void pcr_cyclic(int P, double* A, double* B, double* C, double* D, double* x) {
+  const int i = threadIdx.x;
+  double a = 0, b = 1, c = 0, d = 0;
+  if (i < P) {
+    a = A[i];
+    b = B[i];
+    c = C[i];
+    d = D[i];
   }
-  for (int i = n - 2; i >= 0; --i) {
-    x[i] -= cw[i + 1] * x[i + 1];
-    z[i] -= cw[i + 1] * z[i + 1];
+  for (int st = 1; st < P; st <<= 1) {
+    __syncthreads();
+    if (i < P) {  // publish this level: B holds 1/b
+      A[i] = a;
+      B[i] = 1.0 / b;
+      C[i] = c;
+      D[i] = d;
+    }
+    __syncthreads();
+    if (i < P) {
+      const int im = (i - st) & (P - 1), ip = (i + st) & (P - 1);
+      const double al = -a * B[im], ga = -c * B[ip];
+      const double na = al * A[im], nc = ga * C[ip];
+      b = fma(al, C[im], fma(ga, A[ip], b));
+      d = fma(al, D[im], fma(ga, D[ip], d));
+      a = na;
+      c = nc;
+    }
   }
-  const double fact = (x[0] + beta * x[n - 1] / gamma) / (1.0 + z[0] + beta * z[n - 1] / gamma);
-  for (int i = 0; i < n; ++i) x[i] -= fact * z[i];
+  if (i < P) x[i] = d / (a + b + c);
+  __syncthreads();
 }
 
 // One linearly implicit S^0 step, in place: (I - m2 dt L_E) x = rho with E
@@ -106,8 +118,8 @@ __device__ void cyclic_small(int n, const double* lo, const double* di, const do
 // last row is a separator; thread p eliminates the interior of chunk p
 // (Thomas, three right-hand sides: the data and the couplings to the two
 // neighbouring separators), the separators satisfy a cyclic P x P
-// tridiagonal system (solved by one thread), then every chunk is rebuilt.
-// Scratch: E, cw, y, vl, vr (nx each) and rs (>= 7 * 256 doubles).
+// tridiagonal system (parallel cyclic reduction), then every chunk is
+// rebuilt.  Scratch: E, cw, y, vl, vr (nx each) and rs (>= 7 * 256 doubles).
 __device__ void limit_step_implicit_block(double* rho, double* E, double* cw, double* y, double* vl,
                                           double* vr, double* rs, const MacroArgs& a, double dt,
                                           double* red) {
@@ -148,7 +160,6 @@ __device__ void limit_step_implicit_block(double* rho, double* E, double* cw, do
   double* rC = rs + 512;
   double* rD = rs + 768;
   double* rL = rs + 1024;
-  double* rZ = rs + 1280;
   if (tid < P) {
     const int b0 = (int)(((long long)(tid + 1) * n) / P) - 1;
     const int il = b0 - 1, ir = (b0 + 1 == n) ? 0 : b0 + 1;
@@ -160,8 +171,7 @@ __device__ void limit_step_implicit_block(double* rho, double* E, double* cw, do
     rD[tid] = rho[b0] - lo * y[il] - up * y[ir];
   }
   __syncthreads();
-  if (tid == 0) cyclic_small(P, rA, rB, rC, rD, rL, rs + 1536, rZ);
-  __syncthreads();
+  pcr_cyclic(P, rA, rB, rC, rD, rL);
   if (tid < P) {
     const int a0 = (int)(((long long)tid * n) / P), b0 = (int)(((long long)(tid + 1) * n) / P) - 1;
     const double Lm = rL[tid == 0 ? P - 1 : tid - 1], Lp = rL[tid];
@@ -328,10 +338,12 @@ size_t macro_ws_bytes(int nx, int grid) {
   return macro_fits(nx) ? 0 : (size_t)grid * ((size_t)kScratchArrays * nx + kReducedDoubles) * sizeof(double);
 }
 
+// chunks of the partitioned solve: chunks of about 8 rows (the serial part of
+// each thread), at most 128 (the reduced system's parallel cyclic reduction
+// is then 7 levels deep), at least 4; a power of two
 int coarse_parts(int nx) {
   int P = 4;
-  while (P < 256 && (long long)(2 * P) * (2 * P) <= nx) P *= 2;
-  if (P > nx / 2) P = nx / 2;
+  while (P < 128 && 2 * P * 8 <= nx) P *= 2;
   return P;
 }
 
