@@ -61,7 +61,7 @@ class _PararealCfg(ctypes.Structure):
     _fields_ = [("t_end", ctypes.c_double), ("n_slices", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("coarse_kind", ctypes.c_int32), ("coarse_steps", ctypes.c_int32),
-                ("dt_fine", ctypes.c_double)]
+                ("dt_fine", ctypes.c_double), ("lift_order", ctypes.c_int32)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -92,6 +92,7 @@ def _load():
                 "orc_limit_step_implicit": (None, [P, ctypes.c_double, _D]),
                 "orc_coarse": (None, [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
                 "orc_lift": (None, [P, _D, _D]),
+                "orc_lift_order": (None, [P, ctypes.c_int, _D, _D]),
                 "orc_parareal": (ctypes.c_int, [P, ctypes.POINTER(_PararealCfg), _D, _D, _D, _D]),
                 "orc_sequential": (None, [P, ctypes.POINTER(_PararealCfg), _D, _D, _D]),
             }
@@ -239,40 +240,45 @@ def coarse(p: Params, t_span: float, rho, kind: int = 0, n_sub: int = 1) -> np.n
     return rho
 
 
-def lift(p: Params, rho) -> np.ndarray:
+def lift(p: Params, rho, order: int = 1) -> np.ndarray:
+    """Lifting of order `order` (Def. 1); order 1 is the first-order term
+    alone, orders 2 and 3 add the Chapman-Enskog terms h2, h3."""
     rho = _f64(rho)
     g = np.empty((p.nx, p.nv))
-    _load().orc_lift(ctypes.byref(p._c()), _dptr(rho), _dptr(g))
+    if order <= 1:
+        _load().orc_lift(ctypes.byref(p._c()), _dptr(rho), _dptr(g))
+    else:
+        _load().orc_lift_order(ctypes.byref(p._c()), int(order), _dptr(rho), _dptr(g))
     return g
 
 
-def _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine):
-    return _PararealCfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine)
+def _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order=1):
+    return _PararealCfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order)
 
 
 def parareal(p: Params, rho0, g0, t_end: float, n_slices: int, max_iter: int,
              tol: float = 0.0, coarse_kind: int = 0, coarse_steps: int = 1,
-             dt_fine: float | None = None):
+             dt_fine: float | None = None, lift_order: int = 1):
     """Algorithm 1; returns (rho_slices [(N+1), nx], errors, iterations)."""
     rho0, g0 = _f64(rho0), _f64(g0)
     if dt_fine is None:
         dt_fine = dt_limit(p)
     out = np.empty((n_slices + 1, p.nx))
     err = np.zeros(max(max_iter, 1))
-    c = _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine)
+    c = _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order)
     it = _load().orc_parareal(ctypes.byref(p._c()), ctypes.byref(c), _dptr(rho0),
                               _dptr(g0), _dptr(out), _dptr(err))
     return out, err[:it], it
 
 
 def sequential(p: Params, rho0, g0, t_end: float, n_slices: int,
-               dt_fine: float | None = None) -> np.ndarray:
+               dt_fine: float | None = None, lift_order: int = 1) -> np.ndarray:
     """Sequential fine reference with relifting at every slice boundary."""
     rho0, g0 = _f64(rho0), _f64(g0)
     if dt_fine is None:
         dt_fine = dt_limit(p)
     out = np.empty((n_slices + 1, p.nx))
-    c = _cfg(t_end, n_slices, 0, 0.0, 0, 1, dt_fine)
+    c = _cfg(t_end, n_slices, 0, 0.0, 0, 1, dt_fine, lift_order)
     _load().orc_sequential(ctypes.byref(p._c()), ctypes.byref(c), _dptr(rho0),
                            _dptr(g0), _dptr(out))
     return out

@@ -494,6 +494,61 @@ void orc_lift(const orc_params* p, const double* rho, double* g) {
   free(v); free(w); free(M); free(E); free(J);
 }
 
+/* Lifting of order L (Def. 1): the Chapman-Enskog perturbations h1..hL of
+   the identification in Sec. 2.1 evaluated at the interfaces, summed with
+   weights eps^l, then projected with (I - Pi) so that <g> = 0 exactly.
+   h2 and h3 follow from h^{(l+1)} = -dt h^{(l-1)} - T h^{(l)} with
+   T f = v df/dx + E df/dv, dv M = -v M, and the drift-diffusion closures
+   d(rho)/dt = dJ/dx, dE/dt = J - mean J:
+     h2 = (v^2 - 1) M (dJ/dx - E J)
+     h3 = v M [dJ/dt - (v^2 - 1) dK/dx - E (3 - v^2) K],  K = dJ/dx - E J,
+     dJ/dt = d2J/dx2 - rho (J - mean J) - E dJ/dx. */
+void orc_lift_order(const orc_params* p, int L, const double* rho, double* g) {
+  const int nx = p->nx, nv = p->nv;
+  const double dx = p->x_len / nx, eps = p->eps;
+  double* v = malloc(sizeof(double) * nv);
+  double* w = malloc(sizeof(double) * nv);
+  double* M = malloc(sizeof(double) * nv);
+  orc_velocity_grid(p, v, w, M);
+  double* E = malloc(sizeof(double) * nx);
+  double* J = malloc(sizeof(double) * nx);
+  double* J1 = malloc(sizeof(double) * nx);  /* dJ/dx */
+  double* J2 = malloc(sizeof(double) * nx);  /* d2J/dx2 */
+  double* K = malloc(sizeof(double) * nx);
+  double* K1 = malloc(sizeof(double) * nx);  /* dK/dx */
+  double* h = malloc(sizeof(double) * nv);
+  orc_poisson(p, rho, E);
+  orc_flux_J(p, rho, E, J);
+  orc_fd_derivative(nx, dx, 1, J, J1);
+  orc_fd_derivative(nx, dx, 2, J, J2);
+  for (int i = 0; i < nx; ++i) K[i] = J1[i] - E[i] * J[i];
+  orc_fd_derivative(nx, dx, 1, K, K1);
+  double Jbar = 0.0;
+  for (int i = 0; i < nx; ++i) Jbar += J[i];
+  Jbar /= nx;
+  for (int i = 0; i < nx; ++i) {
+    const double rho_i = 0.5 * (rho[i] + rho[(i + 1) % nx]);
+    const double dtJ = J2[i] - rho_i * (J[i] - Jbar) - E[i] * J1[i];
+    double mean = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      const double v2 = v[j] * v[j];
+      double hj = eps * (-v[j] * M[j] * J[i]);
+      if (L >= 2) hj += eps * eps * (v2 - 1.0) * M[j] * K[i];
+      if (L >= 3)
+        hj += eps * eps * eps * v[j] * M[j] * (dtJ - (v2 - 1.0) * K1[i] - E[i] * (3.0 - v2) * K[i]);
+      h[j] = hj;
+      mean += w[j] * hj;
+    }
+    for (int j = 0; j < nv; ++j) g[(size_t)i * nv + j] = h[j] - mean * M[j];
+  }
+  free(v); free(w); free(M); free(E); free(J); free(J1); free(J2); free(K); free(K1); free(h);
+}
+
+static void relift(const orc_params* p, const orc_parareal_cfg* c, const double* rho, double* g) {
+  if (c->lift_order > 1) orc_lift_order(p, c->lift_order, rho, g);
+  else orc_lift(p, rho, g);
+}
+
 /* ---------------------------------------------------------- parareal ---- */
 
 static int64_t steps_for(double span, double dt_lim) {
@@ -517,7 +572,7 @@ int orc_parareal(const orc_params* p, const orc_parareal_cfg* c,
   double* g = malloc(sizeof(double) * (size_t)nx * nv);
   double* tmp = malloc(sizeof(double) * nx);
 
-  /* first coarse guess (lines 1-6 of the listing) */
+  /* first coarse guess of Algorithm 1 */
   memcpy(rho_slices, rho0, sizeof(double) * nx);
   for (int n = 0; n < N; ++n) {
     memcpy(tmp, rho_slices + (size_t)n * nx, sizeof(double) * nx);
@@ -533,7 +588,7 @@ int orc_parareal(const orc_params* p, const orc_parareal_cfg* c,
       double* r = Frho + (size_t)(n + 1) * nx;
       memcpy(r, rho_slices + (size_t)n * nx, sizeof(double) * nx);
       if (n == 0) memcpy(g, g0, sizeof(double) * (size_t)nx * nv);
-      else orc_lift(p, r, g);
+      else relift(p, c, r, g);
       orc_fine(p, nf, dtf, r, g, NULL, NULL);
     }
     /* sequential correction */
@@ -572,7 +627,7 @@ void orc_sequential(const orc_params* p, const orc_parareal_cfg* c,
     double* r = rho_slices + (size_t)(n + 1) * nx;
     memcpy(r, rho_slices + (size_t)n * nx, sizeof(double) * nx);
     if (n == 0) memcpy(g, g0, sizeof(double) * (size_t)nx * nv);
-    else orc_lift(p, r, g);
+    else relift(p, c, r, g);
     orc_fine(p, nf, dtf, r, g, NULL, NULL);
   }
   free(g);

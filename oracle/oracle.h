@@ -22,8 +22,9 @@
  *
  * Parity unpinned (no closed form or printed value fixes them; any consistent
  * choice passes): the meaning of the adaptation thresholds (literal |R| vs
- * eps^2 |R|), the discrete time derivative of E inside R, and lifting orders
- * above one.
+ * eps^2 |R|) and the discrete time derivative of E inside R.  The lifting
+ * of orders two and three is pinned to its continuous limit and to the
+ * scheme's own relaxed perturbation, not to a printed value.
  */
 #ifndef ORACLE_H
 #define ORACLE_H
@@ -118,6 +119,20 @@ void orc_coarse(const orc_params* p, int kind, int n_sub, double t_span,
    g_{i+1/2,j} = -eps (I - Pi)[xi_j M_j J_{i+1/2}] */
 void orc_lift(const orc_params* p, const double* rho, double* g);
 
+/* lifting of order L = 1, 2, 3 (Def. 1 with the identification of Sec. 2.1,
+   eq. Identification, truncated at L; d_x = d_v = 1):
+     g = (I - Pi)[eps h1 + eps^2 h2 + eps^3 h3]   (terms up to order L)
+     h1_j = -v_j M_j J
+     h2_j = (v_j^2 - 1) M_j K,                      K = dJ/dx - E J
+     h3_j = v_j M_j [dJ/dt - (v_j^2 - 1) dK/dx - E (3 - v_j^2) K]
+   with dtJ = d2J/dx2 - rho (J - mean J) - E dJ/dx (the drift-diffusion
+   closures d(rho)/dt = dJ/dx and dE/dt = J - mean J).  Everything lives at
+   the interfaces: E from the Poisson law, J the S^0 flux, rho the mean of
+   the two neighbouring cells (Sec. 3.3 uses interface averages of the
+   density); x-derivatives are the Table 1 stencils on the interface grid.
+   L = 1 is orc_lift. */
+void orc_lift_order(const orc_params* p, int L, const double* rho, double* g);
+
 typedef struct {
   double t_end;       /* T */
   int32_t n_slices;   /* N_g */
@@ -125,6 +140,7 @@ typedef struct {
   double tol;         /* stop when the successive error is below tol */
   int32_t coarse_kind, coarse_steps;
   double dt_fine;     /* fine step limit; per slice n = ceil(slice/dt_fine) */
+  int32_t lift_order; /* L of the relifting (0 or 1: order one) */
 } orc_parareal_cfg;
 
 /* Algorithm 1 (Sec. 3.3): rho-only parareal with relifting.
@@ -135,7 +151,8 @@ int orc_parareal(const orc_params* p, const orc_parareal_cfg* c,
                  double* err);
 
 /* sequential fine reference of the same problem: rho^{n+1} =
-   F_rho(rho^n, L rho^n) (g0 for the first slice) */
+   F_rho(rho^n, L rho^n) (g0 for the first slice), with the lifting of
+   order c->lift_order */
 void orc_sequential(const orc_params* p, const orc_parareal_cfg* c,
                     const double* rho0, const double* g0, double* rho_slices);
 

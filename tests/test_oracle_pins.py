@@ -339,6 +339,90 @@ def test_lift_carries_no_mass_and_gives_the_fluid_flux():
     assert np.abs((g @ (w * v)) / p.eps + m2 * J).max() < 1e-14 * np.abs(J).max() * 10
 
 
+@pytest.mark.parametrize("L", [2, 3])
+def test_higher_order_lift_carries_no_mass(L):
+    """Def. 1: the lifted perturbation has zero mass for every order."""
+    p = P(nx=64, nv=32, eps=0.05)
+    v, w, M, m2 = O.velocity_grid(p)
+    x = (np.arange(64) + 0.5) / 64
+    g = O.lift(p, 1.0 + 0.3 * np.cos(2 * np.pi * x), L)
+    assert np.abs(g @ w).max() < 1e-16
+
+
+def _ce_terms_continuous(A, xs):
+    """Chapman-Enskog terms of Sec. 2.1 (eq. Identification) for
+    rho = 1 + A cos(2 pi x) on the unit torus, in closed form: the Poisson
+    law E' = rho - 1 with mean-zero E gives E = A sin(2 pi x) / (2 pi);
+    J = rho' - E rho; K = J' - E J; dJ/dt = J'' - rho (J - mean J) - E J'."""
+    x = sp.symbols("x")
+    rho = 1 + A * sp.cos(2 * sp.pi * x)
+    E = A * sp.sin(2 * sp.pi * x) / (2 * sp.pi)
+    J = sp.diff(rho, x) - E * rho
+    Jbar = sp.integrate(J, (x, 0, 1))
+    K = sp.diff(J, x) - E * J
+    dtJ = sp.diff(J, x, 2) - rho * (J - Jbar) - E * sp.diff(J, x)
+    f = {k: sp.lambdify(x, e, "numpy") for k, e in
+         dict(E=E, J=J, K=K, K1=sp.diff(K, x), dtJ=dtJ).items()}
+    return {k: np.broadcast_to(np.asarray(fn(xs), dtype=float), xs.shape) for k, fn in f.items()}
+
+
+def test_higher_order_lift_converges_to_chapman_enskog_terms():
+    """The discrete lifting of order 3 at the interfaces converges, at second
+    order in dx (the interface flux J of S^0 is centred), to
+    (I - Pi)[eps h1 + eps^2 h2 + eps^3 h3] built from the closed-form
+    fields; a dropped term, a wrong sign or coefficient in h2 or h3, or a
+    shifted stencil would leave an O(1) error."""
+    A, eps, nv = 0.3, 0.1, 32
+    errs = []
+    for nx in (64, 128, 256):
+        p = P(nx=nx, nv=nv, eps=eps, rho_bar=1.0)
+        v, w, M, m2 = O.velocity_grid(p)
+        xi = (np.arange(nx) + 1.0) / nx           # interfaces x_{i+1/2}
+        c = _ce_terms_continuous(A, xi)
+        V, Mj = v[None, :], M[None, :]
+        h1 = -V * Mj * c["J"][:, None]
+        h2 = (V * V - 1) * Mj * c["K"][:, None]
+        rho_i = 1 + A * np.cos(2 * np.pi * xi)
+        h3 = V * Mj * (c["dtJ"][:, None] - (V * V - 1) * c["K1"][:, None]
+                       - c["E"][:, None] * (3 - V * V) * c["K"][:, None])
+        h = eps * h1 + eps ** 2 * h2 + eps ** 3 * h3
+        g_cont = h - (h @ w)[:, None] * Mj
+        x = (np.arange(nx) + 0.5) / nx
+        g = O.lift(p, 1 + A * np.cos(2 * np.pi * x), 3)
+        errs.append(np.abs(g - g_cont).max() / np.abs(g_cont).max())
+        del rho_i
+    assert errs[-1] < 2e-4
+    for a, b in zip(errs, errs[1:]):
+        assert 3.5 < a / b < 4.5, errs
+
+
+def _relaxed_gap(eps, L, nx=512, nv=64):
+    """Distance between the perturbation F itself relaxes to and the lifting
+    of order L of F's density: F runs for 20 eps^2 (twenty relaxation times,
+    a^n ~ e^-20, short against the macroscopic time) from (rho, L rho)."""
+    p = P(nx=nx, nv=nv, eps=eps, rho_bar=1.0)
+    x = (np.arange(nx) + 0.5) / nx
+    rho = 1 + 0.3 * np.cos(2 * np.pi * x)
+    dt = O.dt_limit(p)
+    n = int(math.ceil(20 * eps * eps / dt))
+    r, g, _, _ = O.fine(p, n, dt, rho, O.lift(p, rho, L))
+    return np.abs(g - O.lift(p, r, L)).max() / np.abs(g).max()
+
+
+def test_lift_order_matches_the_schemes_relaxed_perturbation():
+    """Chapman-Enskog consistency (Sec. 2.1, Def. 1): the scheme's own
+    relaxed perturbation differs from the lifting of order L by O(eps^L)
+    (relative), so each order gains a factor ~eps, down to the
+    discretisation floor of the upwind transport.  Slopes in eps: 1 for
+    L = 1, 2 for L = 2, more than 2 for L = 3."""
+    gaps = {L: [_relaxed_gap(e, L) for e in (0.02, 0.01)] for L in (1, 2, 3)}
+    slope = {L: math.log2(gaps[L][0] / gaps[L][1]) for L in (1, 2, 3)}
+    assert 0.9 < slope[1] < 1.1, gaps
+    assert 1.8 < slope[2] < 2.2, gaps
+    assert slope[3] > 2.3, gaps
+    assert gaps[1][1] > 10 * gaps[2][1] > 40 * gaps[3][1], gaps
+
+
 # --------------------------------------------------------------- dt rule -
 
 def _jacobian(p, dt, n_eq=1.0, h=1e-7):
@@ -384,14 +468,14 @@ def _parareal_case():
     return w, p
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
-def test_parareal_first_k_slices_equal_sequential(k):
+@pytest.mark.parametrize("k,L", [(1, 1), (2, 1), (3, 1), (2, 2), (2, 3)])
+def test_parareal_first_k_slices_equal_sequential(k, L):
     """After k iterations the first k+1 slice values are the sequential fine
     solution (parareal property, Sec. 3.1), bitwise with the F + (G - G)
-    form of the correction."""
+    form of the correction, for liftings of order L = 1, 2, 3."""
     w, p = _parareal_case()
-    seq = O.sequential(p, w.rho0, w.g0, w.t_end, w.n_slices)
-    out, err, it = O.parareal(p, w.rho0, w.g0, w.t_end, w.n_slices, k)
+    seq = O.sequential(p, w.rho0, w.g0, w.t_end, w.n_slices, lift_order=L)
+    out, err, it = O.parareal(p, w.rho0, w.g0, w.t_end, w.n_slices, k, lift_order=L)
     assert it == k
     assert np.array_equal(out[: k + 1], seq[: k + 1])
     if k < w.n_slices:
