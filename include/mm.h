@@ -114,7 +114,10 @@ typedef struct {
   int32_t coarse_kind; /* G: 0 = linearly implicit S^0, 1 = explicit S^0 */
   int32_t coarse_steps;/* G steps per slice (>= 1); the explicit kind uses
                           max(coarse_steps, the steps its stability needs) */
-  int32_t lift_order;  /* lifting order L of Def. 1; 1 is implemented */
+  int32_t lift_order;  /* lifting order L of Def. 1: 1, 2 or 3 (the
+                          Chapman-Enskog terms h1..hL of Sec. 2.1 at the
+                          interfaces, x-derivatives by Table 1, then the
+                          (I - Pi) projection; see mm_lift) */
   int32_t precision;   /* mm_precision */
   int32_t fine_kernel; /* F implementation: 0 = automatic; 1 = streaming
                           (one CTA per state, g in device memory, every
@@ -125,6 +128,12 @@ typedef struct {
                           and a multiple of 4 * 256 / (nv / 8);
                           MM_ERR_INVALID otherwise).  Automatic picks the
                           resident kernel whenever it applies. */
+  int32_t fine_vpt;    /* velocity nodes per lane of the streaming kernel:
+                          0 = the most that fits (8 in FP32, 4 in FP64, or
+                          fewer when nv requires); 1, 2, 4 or 8 (FP32) / 1,
+                          2, 4 (FP64) forces that lane layout
+                          (MM_ERR_INVALID if nv does not allow it).  The
+                          batch engine always uses the default. */
 } mm_params;
 
 typedef struct mm_ctx mm_ctx;
@@ -228,6 +237,40 @@ MM_API mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, double t_
                                     double* rho_out, void* g_out, uint8_t* mask_out,
                                     mm_fine_stats* stats, void* stream);
 
+/* Result of mm_autotune: the launch shape chosen and every candidate's
+   time (the first 16). */
+typedef struct {
+  int32_t n_candidates;
+  int32_t fine_kernel;       /* chosen: 1 = streaming, 2 = resident */
+  int32_t cluster;           /* chosen CTAs per state (resident), else 1 */
+  int32_t vpt, lanes;        /* chosen lane layout (streaming kernel) */
+  double best_ms;            /* device time of the chosen shape */
+  int32_t cand_kernel[16], cand_cluster[16], cand_vpt[16];
+  double cand_ms[16];
+} mm_tune_result;
+
+/* Autotuner of F's launch shape (the numerical scheme, eq. S^HMM of
+   Sec. 2.3, is unchanged; only the kernel and its decomposition differ, so
+   results agree to rounding).  Times, on the caller's batch, `steps` steps
+   of every shape that suits the context -- the resident kernel with each
+   cluster size 1, 2, 4, 8 its rules allow, the streaming kernel with each
+   lane layout (8, 4, 2 or 1 velocity nodes per lane in FP32; 4, 2, 1 in
+   FP64) -- restricted by params.fine_kernel when that is not 0, and keeps
+   the fastest for every later mm_fine_propagate and parareal_run of this
+   context (mm_query reports it).  The batch engine's work-list kernel is
+   not affected.
+     rho_in, g_in   inputs as for mm_fine_propagate (not modified)
+     rho_out, g_out scratch outputs (must not alias the inputs); they hold
+                    the last candidate's result on return
+     out            NULL or the choice and the candidates' times
+   batch == 0 restores the default choice.  Synchronises the stream.
+   Errors: MM_ERR_INVALID (steps < 1, NULL or aliased arrays, no shape),
+   MM_ERR_UNSTABLE, MM_ERR_CUDA, MM_ERR_OOM; on error the previous choice
+   stays. */
+MM_API mm_status mm_autotune(mm_ctx* ctx, int32_t batch, int32_t steps, const double* rho_in,
+                             const void* g_in, double* rho_out, void* g_out, mm_tune_result* out,
+                             void* stream);
+
 /* G over a span (Sec. 2.3, eq. S^0): coarse_steps linearly implicit steps
    (E frozen from the old density, cyclic tridiagonal solve) or explicit S^0
    steps, for every density of the batch.  rho_in and rho_out may alias.
@@ -235,10 +278,17 @@ MM_API mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, double t_
 MM_API mm_status mm_coarse(mm_ctx* ctx, int32_t batch, double t_span,
                     const double* rho_in, double* rho_out, void* stream);
 
-/* Lifting of order one (Def. 1; identification l = 0 of Sec. 2.1;
-   interface density averaged as in Sec. 3.3):
-   g_{i+1/2,j} = -eps (I - Pi)[xi_j M_j J_{i+1/2}], J from the Poisson law
-   and S^0.  g_out has the context's precision.
+/* Lifting of order L = params.lift_order (Def. 1, Sec. 3.2-3.3): the
+   Chapman-Enskog perturbations of the identification in Sec. 2.1 truncated
+   at order L, evaluated at the interfaces (interface density averaged as in
+   Sec. 3.3), then projected with (I - Pi) so that <g> = 0:
+     g = (I - Pi)[eps h1 + eps^2 h2 + eps^3 h3]   (terms up to order L)
+     h1 = -v M J,  h2 = (v^2 - 1) M K,
+     h3 = v M [dJ/dt - (v^2 - 1) dK/dx - E (3 - v^2) K],
+   K = dJ/dx - E J, dJ/dt = d2J/dx2 - rho (J - mean J) - E dJ/dx; E from
+   the Poisson law, J the S^0 flux, x-derivatives by the Table 1 stencils
+   on the interface grid.  Computed in double; g_out has the context's
+   precision.  parareal_run and the batch engine relift with the same order.
    Errors: MM_ERR_INVALID, MM_ERR_CUDA, MM_ERR_OOM. */
 MM_API mm_status mm_lift(mm_ctx* ctx, int32_t batch, const double* rho, void* g_out,
                   void* stream);

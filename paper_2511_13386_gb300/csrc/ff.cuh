@@ -52,6 +52,22 @@ __device__ __forceinline__ ff ff_add_f(ff a, float b) {
   return fast_two_sum(s.hi, v);
 }
 
+// double-word + double-word, "sloppy" form (Dekker 1971): one TwoSum of the
+// high parts, the low parts added in float.  Its error is bounded in
+// absolute terms, about 2^-47 (|a| + |b|), not relative to the result: what
+// a finite-difference stencil over values of similar size needs, at about
+// half the cost of ff_add.
+__device__ __forceinline__ ff ff_add_abs(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  const float w = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, w);
+}
+__device__ __forceinline__ ff ff_sub_abs(ff a, ff b) {
+  const ff s = two_sum(a.hi, -b.hi);
+  const float w = __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, w);
+}
+
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 

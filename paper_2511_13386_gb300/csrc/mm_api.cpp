@@ -93,13 +93,54 @@ struct mm_ctx {
   mm_params p{};
   int device = 0;
   mmk::VelocityGrid vg;
-  mmk::LaneLayout lay;
+  mmk::LaneLayout lay;       // default streaming layout (the batch engine's)
+  mmk::LaneLayout fine_lay;  // streaming layout of mm_fine_propagate (params.fine_vpt)
   double dt_rule = 0;     // stability limit of the rule at cfl_theta
   double dt_limit = 0;    // limit actually used (params.dt or dt_rule)
   double* d_vtab = nullptr;
   float* d_vtab_f = nullptr;
   Workspace ws;
+  // launch shape of F chosen by mm_autotune (tuned == 0: the defaults)
+  int tuned = 0;
+  int tuned_kernel = 0;       // 1 streaming, 2 resident
+  int tuned_cluster = 0;      // resident: CTAs per state
+  mmk::LaneLayout tuned_lay;  // streaming: lane layout
 };
+
+// ------------------------------------------------------- launch choice ---
+
+namespace {
+struct FineChoice {
+  int kernel = 1;          // 1 streaming, 2 resident
+  int C = 0;               // resident cluster size
+  size_t res_smem = 0;
+  mmk::LaneLayout lay;     // streaming lane layout
+};
+}  // namespace
+
+// The F implementation and launch shape mm_fine_propagate uses: the tuned
+// one, else the resident kernel whenever the shape allows it (unless
+// params.fine_kernel asks for the streaming one), with the default lane
+// layout for the streaming kernel.
+static FineChoice fine_choice(const mm_ctx* c) {
+  const mm_params& p = c->p;
+  const bool fp32 = p.precision == MM_FP32G, adapt = p.adapt != 0;
+  FineChoice f;
+  f.lay = c->fine_lay;
+  if (c->tuned) {
+    f.kernel = c->tuned_kernel;
+    if (f.kernel == 2) {
+      f.C = c->tuned_cluster;
+      f.res_smem = mmk::fine_resident_smem(p.nx, p.nv, fp32, adapt, p.flux_rule, f.C);
+    } else {
+      f.lay = c->tuned_lay;
+    }
+    return f;
+  }
+  if (p.fine_kernel != 1) f.C = mmk::fine_resident_cluster(p.nx, p.nv, fp32, adapt, p.flux_rule, &f.res_smem);
+  f.kernel = f.C ? 2 : 1;
+  return f;
+}
 
 // ----------------------------------------------------------- parameters --
 
@@ -141,10 +182,12 @@ static mmk::VelocityGrid build_velocity_grid(int nv, double v_max) {
   }
   g.m2 = 0.0;
   g.xiM = 0.0;
+  g.mu3 = 0.0;
   for (int j = 0; j < nv; ++j) {
     g.M[j] = exp(-0.5 * g.v[j] * g.v[j]) / Z;
     g.m2 += g.w[j] * g.v[j] * g.v[j] * g.M[j];
     g.xiM += g.w[j] * g.v[j] * g.M[j];
+    g.mu3 += g.w[j] * g.v[j] * g.v[j] * g.v[j] * g.M[j];
   }
   return g;
 }
@@ -180,24 +223,30 @@ static double stability_limit(const mm_params& p, double m2) {
   return lo;
 }
 
+// Lane layout of the streaming kernel with vpt velocity nodes per lane:
+// each half of the velocity grid gets nh = nv / 2 / vpt lanes, padded to a
+// power of two; at most 32 lanes per column.
+static bool layout_for(int nv, int vpt, mmk::LaneLayout* out) {
+  if (nv < 4 || nv % 2 || (nv / 2) % vpt) return false;
+  const int nh = nv / 2 / vpt;
+  int nhp = 1;
+  while (nhp < nh) nhp <<= 1;
+  if (2 * nhp > 32) return false;
+  out->vpt = vpt;
+  out->nh = nh;
+  out->nhp = nhp;
+  out->lanes = 2 * nhp;
+  return true;
+}
+
+static const int kVpt32[] = {8, 4, 2, 1}, kVpt64[] = {4, 2, 1};
+
+// Default layout: the most velocity nodes per lane that works.
 static bool choose_layout(int nv, bool fp32, mmk::LaneLayout* out) {
-  if (nv < 4 || nv % 2) return false;
-  const int cand32[] = {8, 4, 2, 1}, cand64[] = {4, 2, 1};
-  const int* c = fp32 ? cand32 : cand64;
+  const int* c = fp32 ? kVpt32 : kVpt64;
   const int nc = fp32 ? 4 : 3;
-  for (int q = 0; q < nc; ++q) {
-    const int vpt = c[q];
-    if ((nv / 2) % vpt) continue;
-    const int nh = nv / 2 / vpt;
-    int nhp = 1;
-    while (nhp < nh) nhp <<= 1;
-    if (2 * nhp > 32) continue;
-    out->vpt = vpt;
-    out->nh = nh;
-    out->nhp = nhp;
-    out->lanes = 2 * nhp;
-    return true;
-  }
+  for (int q = 0; q < nc; ++q)
+    if (layout_for(nv, c[q], out)) return true;
   return false;
 }
 
@@ -211,12 +260,19 @@ static mm_status validate(const mm_params* p) {
     return mm_fail(MM_ERR_INVALID, "unknown precision");
   if (p->coarse_kind != 0 && p->coarse_kind != 1) return mm_fail(MM_ERR_INVALID, "coarse_kind must be 0 or 1");
   if (p->coarse_steps < 1) return mm_fail(MM_ERR_INVALID, "coarse_steps must be >= 1");
-  if (p->lift_order != 1) return mm_fail(MM_ERR_INVALID, "only lift_order 1 is implemented");
+  if (p->lift_order < 1 || p->lift_order > 3) return mm_fail(MM_ERR_INVALID, "lift_order must be 1, 2 or 3");
   if (p->flux_rule != 0 && p->flux_rule != 1) return mm_fail(MM_ERR_INVALID, "flux_rule must be 0 or 1");
   if (p->dt < 0 || !(p->cfl_theta >= 0)) return mm_fail(MM_ERR_INVALID, "dt and cfl_theta must be >= 0");
   if (p->adapt && (!(p->thr_g >= 0) || !(p->thr_R >= 0)))
     return mm_fail(MM_ERR_INVALID, "thresholds must be >= 0");
   if (p->fine_kernel < 0 || p->fine_kernel > 2) return mm_fail(MM_ERR_INVALID, "fine_kernel must be 0, 1 or 2");
+  if (p->fine_vpt != 0) {
+    mmk::LaneLayout l;
+    const int mx = p->precision == MM_FP32G ? 8 : 4;
+    if (p->fine_vpt < 0 || p->fine_vpt > mx || (p->fine_vpt & (p->fine_vpt - 1)) ||
+        !layout_for(p->nv, p->fine_vpt, &l))
+      return mm_fail(MM_ERR_INVALID, "fine_vpt: no lane layout with that many nodes per lane for this nv");
+  }
   if (p->fine_kernel == 2) {
     size_t sm;
     if (!mmk::fine_resident_cluster(p->nx, p->nv, p->precision == MM_FP32G, p->adapt != 0, p->flux_rule, &sm))
@@ -239,6 +295,8 @@ extern "C" mm_status mm_create(const mm_params* p, const mm_alloc* alloc, mm_ctx
   c->p = *p;
   if (c->p.cfl_theta == 0) c->p.cfl_theta = 0.9;
   c->lay = lay;
+  c->fine_lay = lay;
+  if (p->fine_vpt) layout_for(p->nv, p->fine_vpt, &c->fine_lay);
   if (alloc && alloc->alloc && alloc->free) {
     c->ws.cb = *alloc;
     c->ws.has_cb = true;
@@ -302,14 +360,11 @@ extern "C" mm_status mm_query(const mm_ctx* c, double t_span, mm_info* out) {
   out->b = c->p.eps * (1.0 - out->a);
   const size_t gsz = c->p.precision == MM_FP32G ? 4 : 8;
   out->state_bytes = (size_t)c->p.nx * 8 + (size_t)c->p.nx * c->p.nv * gsz;
-  out->vpt = c->lay.vpt;
-  out->lanes = c->lay.lanes;
-  size_t sm;
-  const int C = c->p.fine_kernel == 1 ? 0
-                                      : mmk::fine_resident_cluster(c->p.nx, c->p.nv, c->p.precision == MM_FP32G,
-                                                                   c->p.adapt != 0, c->p.flux_rule, &sm);
-  out->fine_kernel = C ? 2 : 1;
-  out->cluster = C ? C : 1;
+  const FineChoice f = fine_choice(c);
+  out->vpt = f.lay.vpt;
+  out->lanes = f.lay.lanes;
+  out->fine_kernel = f.kernel;
+  out->cluster = f.kernel == 2 ? f.C : 1;
   return MM_OK;
 }
 
@@ -362,8 +417,9 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
     return st;
 
   const bool adapt = p.adapt != 0;
-  size_t res_smem = 0;
-  const int res_C = p.fine_kernel == 1 ? 0 : mmk::fine_resident_cluster(p.nx, p.nv, fp32, adapt, p.flux_rule, &res_smem);
+  const FineChoice fc = fine_choice(c);
+  const size_t res_smem = fc.res_smem;
+  const int res_C = fc.kernel == 2 ? fc.C : 0;
 
   void* buf1 = nullptr;
   if (!res_C && (st = c->ws.get(WS_GBUF1, gbytes, s, &buf1)) != MM_OK) return st;
@@ -382,9 +438,9 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.nv = p.nv;
   a.batch = batch;
   a.n_steps = n;
-  a.lanes = c->lay.lanes;
-  a.nh = c->lay.nh;
-  a.nhp = c->lay.nhp;
+  a.lanes = fc.lay.lanes;
+  a.nh = fc.lay.nh;
+  a.nhp = fc.lay.nhp;
   a.dt = dt;
   a.dx = p.x_len / p.nx;
   a.inv_dx = 1.0 / a.dx;
@@ -411,9 +467,11 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.vtab = c->d_vtab;
   a.vtab_f = c->d_vtab_f;
   a.xiM = c->vg.xiM;
+  a.mu3 = c->vg.mu3;
+  a.lift_order = c->p.lift_order;
 
-  const size_t colb = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt);
-  const bool in_smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, true) <= 232448;
+  const size_t colb = mmk::fine_column_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
+  const bool in_smem = colb == 0;
   a.col_in_smem = in_smem ? 1 : 0;
   if (!in_smem && !res_C) {
     if ((st = c->ws.get(WS_COLS, colb * batch, s, &a.col_ws)) != MM_OK) return st;
@@ -431,9 +489,9 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, fp32, adapt, in_smem);
+  const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
   cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s)
-                        : mmk::launch_fine(a, c->lay.vpt, fp32, smem, s);
+                        : mmk::launch_fine(a, fc.lay.vpt, fp32, smem, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
   if (stats) cudaEventRecord(e1, s);
 
@@ -488,6 +546,96 @@ extern "C" mm_status mm_fine_propagate(mm_ctx* c, int32_t batch, double t_span, 
                    (cudaStream_t)stream);
 }
 
+// ------------------------------------------------------------ autotune --
+
+// Time every launch shape F can take for this context on the caller's
+// arrays (resident kernel with each cluster size that suits the shape,
+// streaming kernel with each lane layout) and keep the fastest for the
+// context.  Each candidate runs twice (the first run configures the kernel
+// and grows the workspace); the second is timed with events around the
+// kernel.
+extern "C" mm_status mm_autotune(mm_ctx* c, int32_t batch, int32_t steps, const double* rho_in,
+                                 const void* g_in, double* rho_out, void* g_out, mm_tune_result* out,
+                                 void* stream) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (batch == 0) {  // back to the default choice
+    c->tuned = 0;
+    if (out) memset(out, 0, sizeof(*out));
+    return MM_OK;
+  }
+  if (batch < 0 || steps < 1) return mm_fail(MM_ERR_INVALID, "batch must be >= 0 and steps >= 1");
+  if (!rho_in || !g_in || !rho_out || !g_out) return mm_fail(MM_ERR_INVALID, "NULL array");
+  if (g_in == g_out || (const void*)rho_in == (const void*)rho_out)
+    return mm_fail(MM_ERR_INVALID, "mm_autotune: outputs must not alias inputs");
+  if (c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
+    return mm_fail(MM_ERR_UNSTABLE, "params.dt is above the stability limit");
+  cudaSetDevice(c->device);
+  const mm_params& p = c->p;
+  const bool fp32 = p.precision == MM_FP32G, adapt = p.adapt != 0;
+  struct Cand {
+    int kernel, C;
+    mmk::LaneLayout lay;
+    double ms;
+  };
+  std::vector<Cand> cands;
+  if (p.fine_kernel != 1)
+    for (int C = 1; C <= 8; C <<= 1)
+      if (mmk::fine_resident_smem(p.nx, p.nv, fp32, adapt, p.flux_rule, C)) cands.push_back({2, C, c->lay, 0.0});
+  if (p.fine_kernel != 2) {
+    const int* vp = fp32 ? kVpt32 : kVpt64;
+    for (int q = 0; q < (fp32 ? 4 : 3); ++q) {
+      mmk::LaneLayout lay;
+      if (p.fine_vpt && vp[q] != p.fine_vpt) continue;
+      if (layout_for(p.nv, vp[q], &lay)) cands.push_back({1, 0, lay, 0.0});
+    }
+  }
+  if (cands.empty()) return mm_fail(MM_ERR_INVALID, "mm_autotune: no launch shape suits this context");
+  const int old_tuned = c->tuned, old_kernel = c->tuned_kernel, old_C = c->tuned_cluster;
+  const mmk::LaneLayout old_lay = c->tuned_lay;
+  const double dt = c->dt_limit;
+  size_t best = 0;
+  for (size_t q = 0; q < cands.size(); ++q) {
+    c->tuned = 1;
+    c->tuned_kernel = cands[q].kernel;
+    c->tuned_cluster = cands[q].C;
+    c->tuned_lay = cands[q].lay;
+    mm_fine_stats fs;
+    mm_status st = MM_OK;
+    for (int rep = 0; rep < 2 && st == MM_OK; ++rep)
+      st = fine_impl(c, batch, steps, dt, rho_in, g_in, rho_out, g_out, nullptr, p.rho_bar, &fs,
+                     (cudaStream_t)stream);
+    if (st != MM_OK) {
+      c->tuned = old_tuned;
+      c->tuned_kernel = old_kernel;
+      c->tuned_cluster = old_C;
+      c->tuned_lay = old_lay;
+      return st;
+    }
+    cands[q].ms = fs.elapsed_ms;
+    if (cands[q].ms < cands[best].ms) best = q;
+  }
+  c->tuned = 1;
+  c->tuned_kernel = cands[best].kernel;
+  c->tuned_cluster = cands[best].C;
+  c->tuned_lay = cands[best].lay;
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->n_candidates = (int32_t)cands.size();
+    out->fine_kernel = cands[best].kernel;
+    out->cluster = cands[best].kernel == 2 ? cands[best].C : 1;
+    out->vpt = cands[best].lay.vpt;
+    out->lanes = cands[best].lay.lanes;
+    out->best_ms = cands[best].ms;
+    for (size_t q = 0; q < cands.size() && q < 16; ++q) {
+      out->cand_kernel[q] = cands[q].kernel;
+      out->cand_cluster[q] = cands[q].kernel == 2 ? cands[q].C : 1;
+      out->cand_vpt[q] = cands[q].lay.vpt;
+      out->cand_ms[q] = cands[q].ms;
+    }
+  }
+  return MM_OK;
+}
+
 // ------------------------------------------------------ coarse and lift --
 
 static mmk::MacroArgs macro_args(const mm_ctx* c, int batch, double t_span, double rho_bar) {
@@ -501,6 +649,8 @@ static mmk::MacroArgs macro_args(const mm_ctx* c, int batch, double t_span, doub
   a.rho_bar = rho_bar;
   a.eps = c->p.eps;
   a.xiM = c->vg.xiM;
+  a.mu3 = c->vg.mu3;
+  a.lift_order = c->p.lift_order;
   a.coarse_kind = c->p.coarse_kind;
   a.t_span = t_span;
   int steps = c->p.coarse_steps;
@@ -743,9 +893,9 @@ mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out)
   f.g_bytes = (size_t)batch * p.nx * p.nv * (f.fp32 ? 4 : 8);
   f.rho_bytes = (size_t)batch * p.nx * 8;
   const bool adapt = p.adapt != 0;
-  f.col_in_smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, true) <= 232448;
-  f.col_bytes = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt);
-  f.smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, f.col_in_smem);
+  f.col_bytes = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, false);
+  f.col_in_smem = f.col_bytes == 0;
+  f.smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, false);
   FineArgs& a = f.args;
   a.nx = p.nx;
   a.nv = p.nv;
@@ -774,6 +924,8 @@ mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out)
   a.vtab = c->d_vtab;
   a.vtab_f = c->d_vtab_f;
   a.xiM = c->vg.xiM;
+  a.mu3 = c->vg.mu3;
+  a.lift_order = c->p.lift_order;
   a.col_in_smem = f.col_in_smem ? 1 : 0;
   a.col_ws_stride = f.col_in_smem ? 0 : f.col_bytes;
   *out = f;
@@ -824,6 +976,8 @@ mmk::FineArgs mmk::ctx_fine_args(const mm_ctx* c, int64_t n, double dt, double r
   a.vtab = c->d_vtab;
   a.vtab_f = c->d_vtab_f;
   a.xiM = c->vg.xiM;
+  a.mu3 = c->vg.mu3;
+  a.lift_order = c->p.lift_order;
   fine_args_floats(a);
   return a;
 }

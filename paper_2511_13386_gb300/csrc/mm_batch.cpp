@@ -252,7 +252,7 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
         cost.push_back((double)v->nf * v->nx * v->nv);
       }
       ws_g = std::max(ws_g, (size_t)v->nx * v->nv * (fp32 ? 4 : 8));
-      ws_col = std::max(ws_col, mmk::fine_column_bytes(v->nx, v->nv, v->lanes, fp32, adapt));
+      ws_col = std::max(ws_col, mmk::fine_column_bytes(v->nx, v->nv, v->lanes, fp32, adapt, true));
       smem_in = std::max(smem_in, mmk::fine_smem_bytes(v->nx, v->nv, v->lanes, fp32, adapt, true));
     }
     if (items.empty()) continue;
@@ -262,11 +262,10 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     std::vector<mmk::FineListItem> sorted(items.size());
     for (size_t q = 0; q < order.size(); ++q) sorted[q] = items[order[q]];
-    const bool col_in_smem = smem_in <= 200 * 1024;
     ws_g = (ws_g + 255) & ~size_t(255);
     ws_col = (ws_col + 255) & ~size_t(255);
     const int grid = (int)std::min<size_t>(sorted.size(), (size_t)b->n_sm);
-    const size_t per_cta = 2 * ws_g + (col_in_smem ? 0 : ws_col);
+    const size_t per_cta = 2 * ws_g + ws_col;
     if ((st = b->grow(b->fine_ws, per_cta * grid, s)) != MM_OK) return st;
     const size_t tb = sizeof(mmk::FineListSolve) * tab.size();
     if ((st = b->grow(b->tables, tb, s)) != MM_OK) return st;
@@ -286,8 +285,7 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
     L.ws = (unsigned char*)b->fine_ws.p;
     L.ws_g = ws_g;
     L.ws_col = ws_col;
-    const size_t smem = col_in_smem ? smem_in : mmk::fine_smem_bytes(1, 1, 1, fp32, adapt, false);
-    e = mmk::launch_fine_list(L, fp32, adapt, col_in_smem, smem, s);
+    e = mmk::launch_fine_list(L, fp32, adapt, smem_in, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "batch: fine work list launch");
     ++b->fine_launches;
     // the host tables are reused by the next class: wait for this launch's

@@ -14,6 +14,7 @@
 // of the serial chains, not the operation count, the cost.
 #include <math.h>
 
+#include "lift.cuh"
 #include "mm_internal.h"
 
 namespace mmk {
@@ -235,15 +236,25 @@ __global__ void lift_kernel(MacroArgs a, const double* rho, G* g, double* gws, i
     S.s1[i] = (r1 - r0) * a.inv_dx - S.s0[i] * 0.5 * (r0 + r1);
   }
   __syncthreads();
-  // g = -eps (xi_j M_j - <xi M> M_j) J_i
   const double* vM = a.vtab + 2 * nv;  // v_j M_j
   const double* Mj = a.vtab + 1 * nv;
+  const double* vj = a.vtab + 5 * nv;
   G* gb = g + (size_t)blockIdx.x * nx * nv;
   const size_t n = (size_t)nx * nv;
+  if (a.lift_order <= 1) {  // g = -eps (xi_j M_j - <xi M> M_j) J_i
+    for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
+      const int i = (int)(q / nv), j = (int)(q % nv);
+      const double J = S.s1[i];
+      gb[q] = (G)(-a.eps * (vM[j] * J - a.xiM * J * Mj[j]));
+    }
+    return;
+  }
+  // orders two and three: K -> s4, dK -> s2, dtJ -> s3
+  lift_fields(S.w, S.s0, S.s1, S.s4, S.s2, S.s3, nx, a.inv_dx, red);
+  const LiftConsts lc{a.lift_order, a.eps, a.xiM, a.m2, a.mu3};
   for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
     const int i = (int)(q / nv), j = (int)(q % nv);
-    const double J = S.s1[i];
-    gb[q] = (G)(-a.eps * (vM[j] * J - a.xiM * J * Mj[j]));
+    gb[q] = (G)lift_value(lc, vj[j], Mj[j], S.s0[i], S.s1[i], S.s4[i], S.s2[i], S.s3[i]);
   }
 }
 

@@ -36,6 +36,7 @@
 #include <stdio.h>
 
 #include "ff.cuh"
+#include "lift.cuh"
 #include "mm_internal.h"
 
 namespace mmk {
@@ -108,50 +109,92 @@ struct MP<float> {
 
 // ------------------------------------------------------- column arrays ---
 
-// Offsets of the per-state column arrays; identical on host and device.
+// Per-state column arrays.  They are placed in shared memory in this
+// priority order while they fit the kernel's budget; the rest go to a
+// per-state block of global memory (one for every state whose column arrays
+// do not fit).  The placement is a function of (nx, precision, adaptation,
+// budget), computed identically on the host and the device.
+enum ColField {
+  F_BASE,   // R [kFineThreads]: per-thread prefix bases of the Poisson law;
+            //   then int [rows][warps] counts / offsets of the compaction
+  F_PAR,    // G [nx][4]: E+/dv, E-/dv, P = <X>, J per interface (sweep constants)
+  F_LIST,   // int [nx]: interfaces the sweep writes (adaptation)
+  F_KIN0, F_KIN1, F_KIN2, F_CELL0, F_CELL1,  // uint8 [nx] status flags (adaptation)
+  F_RHO,    // R [nx]: density (float-float or double)
+  F_JD,     // 8 B [nx]: centred flux of the criteria (adaptation)
+  F_ED,     // 8 B [nx]: field of the criteria (adaptation)
+  F_PART,   // G [nx][4]: sums of w v g over the negative / positive velocities
+            //   (value and compensation each), one record per interface
+  F_N2,     // G [nx]: <g^2> per interface (adaptation)
+  F_ENDS,   // G [nx][4]: g at the two lowest and the two highest nodes
+  F_RD,     // 8 B [nx]: first derivative of the density (adaptation)
+  F_S,      // R [nx]: prefix sums of the Poisson law
+  F_COUNT
+};
+
 struct ColLayout {
-  size_t rho, S, jg, mp, mm, part, n2, ends, par, list, ed, rd, jd, cell0, cell1, kin0, kin1, kin2, total;
+  size_t off[F_COUNT];
+  unsigned smem_mask;     // bit f set: field f lives in shared memory
+  size_t smem_total;      // bytes in shared memory
+  size_t glob_total;      // bytes in global memory per state
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline ColLayout col_layout(int nx, int lanes, int gbytes, bool adapt) {
+// Shared-memory budget of the column arrays: the fine kernel's dynamic
+// shared memory (232,448 B) or the list kernel's (200 KiB), less the
+// reduction scratch.
+constexpr int kRedSlots = 160;  // reduction scratch entries (8 bytes each)
+constexpr size_t kColBudgetFine = 232448 - 8 * kRedSlots;
+constexpr size_t kColBudgetList = 200 * 1024 - 8 * kRedSlots;
+
+__host__ __device__ inline ColLayout col_layout(int nx, int gbytes, bool adapt, size_t budget) {
+  const size_t n = nx, a = adapt ? 1 : 0;
+  size_t sz[F_COUNT];
+  const size_t rows = (n + kFineThreads - 1) / kFineThreads;
+  sz[F_BASE] = 8 * (size_t)kFineThreads > 4 * rows * (kFineThreads / 32) ? 8 * (size_t)kFineThreads
+                                                                          : 4 * rows * (kFineThreads / 32);
+  sz[F_PAR] = gbytes * 4 * n;
+  sz[F_LIST] = a * 4 * n;
+  sz[F_KIN0] = sz[F_KIN1] = sz[F_KIN2] = sz[F_CELL0] = sz[F_CELL1] = a * n;
+  sz[F_RHO] = 8 * n;
+  sz[F_JD] = a * 8 * n;
+  sz[F_ED] = a * 8 * n;
+  sz[F_PART] = gbytes * 4 * n;
+  sz[F_N2] = a * gbytes * n;
+  sz[F_ENDS] = gbytes * 4 * n;
+  sz[F_RD] = a * 8 * n;
+  sz[F_S] = 8 * n;
   ColLayout L;
-  const size_t n = nx;
-  size_t o = 0;
-  L.rho = o;  o = al16(o + 8 * n);
-  L.S = o;    o = al16(o + 8 * n);
-  L.jg = o;   o = al16(o + gbytes * n);
-  L.mp = o;   o = al16(o + gbytes * n);
-  L.mm = o;   o = al16(o + gbytes * n);
-  L.part = o; o = al16(o + gbytes * n * lanes);
-  L.ends = o; o = al16(o + gbytes * n * 4);
-  L.par = o;  o = al16(o + gbytes * n * 4);
-  L.n2 = o;   if (adapt) o = al16(o + gbytes * n * lanes);
-  L.list = o; if (adapt) o = al16(o + 4 * n);
-  L.ed = o;   if (adapt) o = al16(o + 8 * n);
-  L.rd = o;   if (adapt) o = al16(o + 8 * n);
-  L.jd = o;   if (adapt) o = al16(o + 8 * n);
-  L.cell0 = o; if (adapt) o = al16(o + n);
-  L.cell1 = o; if (adapt) o = al16(o + n);
-  L.kin0 = o;  if (adapt) o = al16(o + n);
-  L.kin1 = o;  if (adapt) o = al16(o + n);
-  L.kin2 = o;  if (adapt) o = al16(o + n);
-  L.total = o;
+  L.smem_mask = 0;
+  L.smem_total = 0;
+  L.glob_total = 0;
+  for (int f = 0; f < F_COUNT; ++f) {
+    const size_t b = al16(sz[f]);
+    if (L.smem_total + b <= budget) {
+      L.off[f] = L.smem_total;
+      L.smem_total += b;
+      L.smem_mask |= 1u << f;
+    }
+  }
+  for (int f = 0; f < F_COUNT; ++f) {
+    if (L.smem_mask & (1u << f)) continue;
+    L.off[f] = L.glob_total;
+    L.glob_total += al16(sz[f]);
+  }
   return L;
 }
 
-constexpr int kRedSlots = 160;  // reduction scratch entries (8 bytes each)
-
-size_t fine_column_bytes(int nx, int nv, int lanes, bool fp32, bool adapt) {
+size_t fine_column_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool list) {
   (void)nv;
-  return col_layout(nx, lanes, fp32 ? 4 : 8, adapt).total;
+  (void)lanes;
+  return col_layout(nx, fp32 ? 4 : 8, adapt, list ? kColBudgetList : kColBudgetFine).glob_total;
 }
 
-size_t fine_smem_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool col_in_smem) {
-  size_t s = 8 * (size_t)kRedSlots;
-  if (col_in_smem) s += fine_column_bytes(nx, nv, lanes, fp32, adapt);
-  return s;
+size_t fine_smem_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool list) {
+  (void)nv;
+  (void)lanes;
+  return 8 * (size_t)kRedSlots + col_layout(nx, fp32 ? 4 : 8, adapt, list ? kColBudgetList : kColBudgetFine).smem_total;
 }
 
 // -------------------------------------------------------- vector access ---
@@ -222,31 +265,18 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return t;
 }
 
-// Exclusive block scan of ints a (returned) with block totals of a and b.
-__device__ __forceinline__ int block_scan2_i(int a, int b, int* red, int* tot_a, int* tot_b) {
+// Block sum of float-float values (absolute-error additions).
+__device__ __forceinline__ ff block_sum_ff(ff v, double* red) {
+  for (int m = 16; m > 0; m >>= 1) v = ff_add_abs(v, ff_shfl_xor(v, m));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  int inc = a;
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, inc, d);
-    if (l >= d) inc += t;
-  }
-  int bs = b;
-  for (int m = 16; m > 0; m >>= 1) bs += __shfl_xor_sync(0xffffffffu, bs, m);
+  ff* r = reinterpret_cast<ff*>(red);
   __syncthreads();
-  if (l == 31) red[w] = inc;
-  if (l == 0) red[32 + w] = bs;
+  if (l == 0) r[w] = v;
   __syncthreads();
-  int off = 0, ta = 0, tb = 0;
-  const int nw = blockDim.x >> 5;
-  for (int q = 0; q < nw; ++q) {
-    if (q < w) off += red[q];
-    ta += red[q];
-    tb += red[32 + q];
-  }
+  ff t = {0.f, 0.f};
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = ff_add_abs(t, r[q]);
   __syncthreads();
-  *tot_a = ta;
-  *tot_b = tb;
-  return off + inc - a;
+  return t;
 }
 
 // ------------------------------------------------------------ the kernel --
@@ -254,49 +284,50 @@ __device__ __forceinline__ int block_scan2_i(int a, int b, int* red, int* tot_a,
 template <class G>
 struct Cols {
   using R = typename MP<G>::R;
-  R *rho, *S;
-  G *jg, *mp, *mm, *part, *n2, *ends, *par;
+  R *rho, *S, *base;
+  G *part, *n2, *ends, *par;
   int* list;
   double *ed, *rd, *jd;
   uint8_t *cell0, *cell1, *kin0, *kin1, *kin2;
 };
 
 template <class G>
-__device__ __forceinline__ Cols<G> carve(unsigned char* base, int nx, int lanes, bool adapt) {
+__device__ __forceinline__ Cols<G> carve(unsigned char* sbase, unsigned char* gbase, int nx, bool adapt,
+                                         size_t budget) {
   using R = typename MP<G>::R;
-  const ColLayout L = col_layout(nx, lanes, sizeof(G), adapt);
+  const ColLayout L = col_layout(nx, sizeof(G), adapt, budget);
+  auto at = [&](int f) { return ((L.smem_mask >> f) & 1u ? sbase : gbase) + L.off[f]; };
   Cols<G> c;
-  c.rho = reinterpret_cast<R*>(base + L.rho);
-  c.S = reinterpret_cast<R*>(base + L.S);
-  c.jg = reinterpret_cast<G*>(base + L.jg);
-  c.mp = reinterpret_cast<G*>(base + L.mp);
-  c.mm = reinterpret_cast<G*>(base + L.mm);
-  c.part = reinterpret_cast<G*>(base + L.part);
-  c.n2 = reinterpret_cast<G*>(base + L.n2);
-  c.ends = reinterpret_cast<G*>(base + L.ends);
-  c.par = reinterpret_cast<G*>(base + L.par);
-  c.list = reinterpret_cast<int*>(base + L.list);
-  c.ed = reinterpret_cast<double*>(base + L.ed);
-  c.rd = reinterpret_cast<double*>(base + L.rd);
-  c.jd = reinterpret_cast<double*>(base + L.jd);
-  c.cell0 = base + L.cell0;
-  c.cell1 = base + L.cell1;
-  c.kin0 = base + L.kin0;
-  c.kin1 = base + L.kin1;
-  c.kin2 = base + L.kin2;
+  c.rho = reinterpret_cast<R*>(at(F_RHO));
+  c.S = reinterpret_cast<R*>(at(F_S));
+  c.base = reinterpret_cast<R*>(at(F_BASE));
+  c.part = reinterpret_cast<G*>(at(F_PART));
+  c.n2 = reinterpret_cast<G*>(at(F_N2));
+  c.ends = reinterpret_cast<G*>(at(F_ENDS));
+  c.par = reinterpret_cast<G*>(at(F_PAR));
+  c.list = reinterpret_cast<int*>(at(F_LIST));
+  c.ed = reinterpret_cast<double*>(at(F_ED));
+  c.rd = reinterpret_cast<double*>(at(F_RD));
+  c.jd = reinterpret_cast<double*>(at(F_JD));
+  c.cell0 = at(F_CELL0);
+  c.cell1 = at(F_CELL1);
+  c.kin0 = at(F_KIN0);
+  c.kin1 = at(F_KIN1);
+  c.kin2 = at(F_KIN2);
   return c;
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Lifting of order one (Def. 1, identification l = 0 of Sec. 2.1) of one
-// density into g, by the whole block, in double: the Poisson law of S^MM
-// (prefix sum, mean-zero gauge), J of S^0, then
-// g_{i+1/2,j} = -eps (xi_j M_j - <xi M> M_j) J_{i+1/2}.  E and J use the
-// first 16 nx bytes of `scratch`.
+// Lifting of order L (Def. 1) of one density into g, by the whole block, in
+// double: the Poisson law of S^MM (prefix sum, mean-zero gauge), J of S^0,
+// then for L = 1 g_{i+1/2,j} = -eps (xi_j M_j - <xi M> M_j) J_{i+1/2}, and
+// for L = 2, 3 the higher Chapman-Enskog terms of lift.cuh.  E and J use
+// the first 16 nx bytes of `scratch`; orders two and three also use
+// scratch2 (16 nx bytes: K, dK) and scratch3 (8 nx bytes: dtJ).
 template <class G>
 __device__ void lift_block(const FineArgs& A, const double* rho, double rb, G* g, unsigned char* scratch,
-                           double* red) {
+                           unsigned char* scratch2, unsigned char* scratch3, double* red) {
   const int nx = A.nx, nv = A.nv, T = blockDim.x, tid = threadIdx.x;
   double* E = reinterpret_cast<double*>(scratch);
   double* J = E + nx;
@@ -338,39 +369,63 @@ __device__ void lift_block(const FineArgs& A, const double* rho, double rb, G* g
   const double* vM = A.vtab + 2 * nv;
   const double* Mj = A.vtab + 1 * nv;
   const unsigned n = (unsigned)nx * (unsigned)nv;
+  if (A.lift_order <= 1) {
+    for (unsigned q = tid; q < n; q += T) {
+      const unsigned i = q / (unsigned)nv, j = q - i * (unsigned)nv;
+      const double Ji = J[i];
+      g[q] = (G)(-A.eps * (vM[j] * Ji - A.xiM * Ji * Mj[j]));
+    }
+    __syncthreads();
+    return;
+  }
+  double* K = reinterpret_cast<double*>(scratch2);
+  double* dK = K + nx;
+  double* dtJ = reinterpret_cast<double*>(scratch3);
+  lift_fields(rho, E, J, K, dK, dtJ, nx, A.inv_dx, red);
+  const double* vj = A.vtab + 5 * nv;
+  const LiftConsts lc{A.lift_order, A.eps, A.xiM, A.m2, A.mu3};
   for (unsigned q = tid; q < n; q += T) {
     const unsigned i = q / (unsigned)nv, j = q - i * (unsigned)nv;
-    const double Ji = J[i];
-    g[q] = (G)(-A.eps * (vM[j] * Ji - A.xiM * Ji * Mj[j]));
+    g[q] = (G)lift_value(lc, vj[j], Mj[j], E[i], J[i], K[i], dK[i], dtJ[i]);
   }
   __syncthreads();
 }
 
 // F for one state: n_steps steps from (rin, gin); gin == nullptr lifts the
 // density first.  buf0/buf1 are the two step buffers (the last step writes
-// buf0); colbase holds the column arrays (shared or global memory).
-template <class G, int VPT, bool ADAPT, bool CSMEM>
+// buf0); the column arrays are carved from colsmem (shared memory, up to
+// `budget` bytes) and colglob (global memory, the fields that do not fit).
+template <class G, int VPT, bool ADAPT>
 __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin, const G* gin, G* buf0, G* buf1,
                                            double* rout, uint8_t* mout, unsigned char* smem,
-                                           unsigned char* colbase) {
+                                           unsigned char* colsmem, unsigned char* colglob, size_t budget) {
   using M = MP<G>;
   using R = typename M::R;
-  using Acc = typename M::A;
 
   const int tid = threadIdx.x;
   const int nx = A.nx, nv = A.nv, Lg = A.lanes;
   constexpr int T = kFineThreads;
 
   double* red = reinterpret_cast<double*>(smem);
+  Cols<G> C = carve<G>(colsmem, colglob, nx, ADAPT, budget);
   if (gin == nullptr) {  // the lifted density goes where the first step does not write
     G* lifted = (A.n_steps & 1) ? buf1 : buf0;
-    lift_block<G>(A, rin, A.rho_bar, lifted, colbase, red);
+    // E and J of the lifting use the sweep-constant array, K, dK and dtJ
+    // the moment records and the end values (16 nx bytes or more each),
+    // which the prologue has not written yet
+    lift_block<G>(A, rin, A.rho_bar, lifted, reinterpret_cast<unsigned char*>(C.par),
+                  reinterpret_cast<unsigned char*>(C.part), reinterpret_cast<unsigned char*>(C.ends), red);
     gin = lifted;
   }
-  Cols<G> C = carve<G>(colbase, nx, Lg, ADAPT);
 
-  // ---- ownership of cells in the macro phase
-  const int cpt = (nx + T - 1) / T;
+  // ---- ownership of cells in the macro phase: interleaved (cell c by
+  // thread c % T, so that a warp touches consecutive cells: conflict-free
+  // shared memory, coalesced global memory) everywhere except the first
+  // pass of the Poisson prefix sum, where thread t owns the contiguous chunk
+  // [t cpt, (t+1) cpt) with cpt a power of two
+  int lcpt = 0;
+  while ((T << lcpt) < nx) ++lcpt;
+  const int cpt = 1 << lcpt;
   const int c0 = min(tid * cpt, nx), c1 = min(c0 + cpt, nx);
 
   // ---- lane layout of the sweep
@@ -414,7 +469,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   double rb = A.rho_bar;
   {
     double s = 0.0;
-    for (int c = c0; c < c1; ++c) {
+    for (int c = tid; c < nx; c += T) {
       const double r = rin[c];
       C.rho[c] = M::c(r);
       s += r;
@@ -423,50 +478,79 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   }
   const R Rrb = M::c(rb);
 
-  for (int i = grp; i < nx; i += ngrp) {
+  // Sums of the lane partials of one interface column over each half of the
+  // lane group (negative / positive velocities), by shuffles, with a
+  // compensation term in the FP32 path (two-sum at every level); lane 0 of
+  // the group stores {pos, pos err, neg, neg err} and the norm.  Every
+  // thread calls it with warp-uniform control flow; `valid` only gates the
+  // store.
+  auto reduce_store = [&](int i, bool valid, G p, G q) {
+    G pe = G(0);
+    for (int m = A.nhp >> 1; m >= 1; m >>= 1) {
+      const G op = __shfl_xor_sync(0xffffffffu, p, m);
+      if constexpr (sizeof(G) == 4) {
+        const G oe = __shfl_xor_sync(0xffffffffu, pe, m);
+        const ff t = two_sum(p, op);
+        p = t.hi;
+        pe = __fadd_rn(__fadd_rn(pe, oe), t.lo);
+      } else {
+        p += op;
+      }
+      if constexpr (ADAPT) q += __shfl_xor_sync(0xffffffffu, q, m);
+    }
+    const int src = warp_base + A.nhp;
+    const G pp = __shfl_sync(0xffffffffu, p, src);
+    G ppe = G(0), qq = G(0);
+    if constexpr (sizeof(G) == 4) ppe = __shfl_sync(0xffffffffu, pe, src);
+    if constexpr (ADAPT) qq = __shfl_sync(0xffffffffu, q, src);
+    if (valid && lig == 0) {
+      G* pr = C.part + 4 * (unsigned)i;
+      if constexpr (sizeof(G) == 4) {
+        *reinterpret_cast<float4*>(pr) = make_float4(pp, ppe, p, pe);
+      } else {
+        pr[0] = pp; pr[1] = ppe; pr[2] = p; pr[3] = pe;
+      }
+      if constexpr (ADAPT) C.n2[i] = q + qq;
+    }
+  };
+  // m+ = <v^+ g>, m- = <v^- g> of an interface from its record
+  auto mplus = [&](int c) { return C.part[4 * c] + C.part[4 * c + 1]; };
+  auto mminus = [&](int c) { return -(C.part[4 * c + 2] + C.part[4 * c + 3]); };
+
+  for (int base = 0; base < nx; base += ngrp) {  // warp-uniform trip count
+    const int i = base + grp;
+    const bool valid = i < nx;
     G w1[VPT];
 #pragma unroll
     for (int k = 0; k < VPT; ++k) w1[k] = G(0);
-    if (active) vload<G, VPT>(w1, gin + (size_t)i * nv + j0);
+    if (active && valid) vload<G, VPT>(w1, gin + (size_t)i * nv + j0);
     G p = 0, q = 0;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
       p += wv[k] * w1[k];
       if constexpr (ADAPT) q += wj[k] * w1[k] * w1[k];
     }
-    C.part[(size_t)i * Lg + lig] = p;
-    if constexpr (ADAPT) C.n2[(size_t)i * Lg + lig] = q;
-    if constexpr (VPT >= 2) {
-      if (first_lane) { C.ends[4 * i + 0] = w1[0]; C.ends[4 * i + 1] = w1[1]; }
-      if (last_lane) { C.ends[4 * i + 2] = w1[VPT - 2]; C.ends[4 * i + 3] = w1[VPT - 1]; }
-    } else {
-      if (end_slot >= 0) C.ends[4 * i + end_slot] = w1[0];
+    reduce_store(i, valid, p, q);
+    if (valid) {
+      if constexpr (VPT >= 2) {
+        if (first_lane) { C.ends[4 * i + 0] = w1[0]; C.ends[4 * i + 1] = w1[1]; }
+        if (last_lane) { C.ends[4 * i + 2] = w1[VPT - 2]; C.ends[4 * i + 3] = w1[VPT - 1]; }
+      } else {
+        if (end_slot >= 0) C.ends[4 * i + end_slot] = w1[0];
+      }
     }
   }
   if constexpr (ADAPT) {
-    for (int c = c0; c < c1; ++c) { C.kin1[c] = 1; C.kin2[c] = 1; }
+    for (int c = tid; c < nx; c += T) { C.kin1[c] = 1; C.kin2[c] = 1; }
   }
   __syncthreads();
-
-  // moments m+- of the current g from the lane partials (own cells)
-  auto moments = [&](int c) {
-    G sp = 0, sm = 0;
-    const G* pp = C.part + c * Lg;
-    for (int l = 0; l < Lg; ++l) {
-      if (l >= A.nhp) sp += pp[l];
-      else sm += pp[l];
-    }
-    C.mp[c] = sp;
-    C.mm[c] = -sm;
-  };
-  for (int c = c0; c < c1; ++c) moments(c);
 
   uint8_t* cell_cur = C.cell0;   // s^n
   uint8_t* cell_nxt = C.cell1;   // s^{n+1}
   uint8_t* kin_cur = C.kin0;     // interface flags under s^n
   uint8_t* kin_prev = C.kin1;    // under s^{n-1}
   uint8_t* kin_prev2 = C.kin2;   // under s^{n-2}
-  int* ired = reinterpret_cast<int*>(red);
+  int* rint = reinterpret_cast<int*>(red) + 300;  // [0] write count, [1] kinetic count
   int count = nx;                // interfaces to write this step
   long long kin_total = 0;       // kinetic interfaces summed over steps (thread 0)
   const int w = tid >> 5, l = tid & 31;
@@ -474,6 +558,12 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   // ------------------------------------------------------------ macro A --
   // E, J, criteria/status, write list and sweep constants for step n.
   auto macro_A = [&](bool initial) {
+    // the density was last written with interleaved ownership (macro_C or
+    // the prologue); the first Poisson pass reads it in contiguous chunks
+    __syncthreads();
+    if constexpr (ADAPT) {
+      if (tid == 0) rint[1] = 0;  // kinetic-interface count of this step
+    }
     // Poisson law: S_c = sum_{m<=c} (rho_m - rho_bar) dx ; E = S - mean(S),
     // with mean(S) = sum_m (nx - m) d_m / nx.
     R t1 = M::zero(), t2 = M::zero();
@@ -517,95 +607,195 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       if (l == 0) rr[96] = M::mul(u, Rinv_nx);
     }
     __syncthreads();
-    const R base = M::add(rr[64 + w], ex_lane);
+    C.base[tid] = M::add(rr[64 + w], ex_lane);   // prefix before this thread's chunk
     const R meanS = rr[96];
+    __syncthreads();
     G* eg = C.par;  // E^n goes through the par array's first slot first
-    for (int c = c0; c < c1; ++c) {
-      const R E = M::sub(M::add(base, C.S[c]), meanS);
+    for (int c = tid; c < nx; c += T) {
+      const R E = M::sub(M::add(C.base[c >> lcpt], C.S[c]), meanS);
       eg[4 * c + 3] = (G)M::tog(E);          // temporary: E in slot 3
-      if constexpr (ADAPT) { C.ed[c] = M::tod(E); C.rd[c] = M::tod(C.rho[c]); }
+      if constexpr (ADAPT) {
+        if constexpr (sizeof(G) == 4) reinterpret_cast<ff*>(C.ed)[c] = E;
+        else { C.ed[c] = E; C.rd[c] = C.rho[c]; }
+      }
     }
     __syncthreads();  // rho final for this step; E of all cells visible
 
     if constexpr (ADAPT) {
-      // criteria of Sec. 2.2 in double: remainder R (eq. Remainder with
-      // Table 1), interface norms ||g||_2; status update of Sec. 2.3.
-      const double inv_dx = A.inv_dx;
-      auto rho_d = [&](int c) { return C.rd[wrapi(c, nx)]; };
-      auto E_d = [&](int c) { return C.ed[wrapi(c, nx)]; };
-      double jsum = 0.0;
-      for (int c = c0; c < c1; ++c) {
-        double d1 = 0.0;
-        for (int k = -3; k <= 3; ++k) d1 += kFD[0][k + 3] * rho_d(c + k);
-        d1 *= inv_dx;
-        const double Ec = 0.5 * (E_d(c - 1) + E_d(c));
-        C.jd[c] = d1 - Ec * rho_d(c);
-        jsum += C.jd[c];
-      }
-      const double meanJ = block_sum_d(jsum, red) / nx;  // (syncs: Jc visible)
-      const double r2 = 1.0 / (A.dx * A.dx), r3 = r2 / A.dx;
-      for (int c = c0; c < c1; ++c) {
-        double d1r = 0.0, d1J = 0.0, d2J = 0.0, d3J = 0.0;
-        for (int k = -3; k <= 3; ++k) {
-          const double jk = C.jd[wrapi(c + k, nx)];
-          d1r += kFD[0][k + 3] * rho_d(c + k);
-          d1J += kFD[0][k + 3] * jk;
-          d2J += kFD[1][k + 3] * jk;
-          d3J += kFD[2][k + 3] * jk;
+      // criteria of Sec. 2.2 and status update of Sec. 2.3: the remainder R
+      // (eq. Remainder with the Table 1 stencils) and the interface norms
+      // ||g||_2.  FP64 path in double; FP32 path in float-float (below).
+      if constexpr (sizeof(G) == 4) {
+        // FP32 path.  GB300 issues FP64 at 1/64 of the FP32 rate, and R is a
+        // fourth derivative of the density: its stencils cancel about
+        // 1/dx^4 ~ 1e14 of the inputs' size, so plain float is useless and
+        // double costs more than the whole g sweep.  The stencil sums run
+        // in float-float (~2^-47 absolute error, R accurate to ~1e-5 of the
+        // thresholds used); the combination of the cancelled sums into R,
+        // and the norms (compared squared), run in float.  Table 1 rows are
+        // applied with integer weights: D1 f = (45 e1 - 9 e2 + e3) / 60,
+        // D2 f = (270 s1 - 27 s2 + 2 s3 - 490 f0) / 180,
+        // D3 f = (-13 e1 + 8 e2 - e3) / 8, with e_k = f_{+k} - f_{-k},
+        // s_k = f_{+k} + f_{-k} (then divided by dx^d).
+        ff* Ef = reinterpret_cast<ff*>(C.ed);
+        ff* Df = reinterpret_cast<ff*>(C.rd);
+        ff* Jf = reinterpret_cast<ff*>(C.jd);
+        const ff k1 = {A.f_k1, A.f_k1_lo};
+        auto rho_f = [&](int c) { return C.rho[wrapi(c, nx)]; };
+        ff jsum = {0.f, 0.f};
+        for (int c = tid; c < nx; c += T) {
+          const ff e1 = ff_sub_abs(rho_f(c + 1), rho_f(c - 1));
+          const ff e2 = ff_sub_abs(rho_f(c + 2), rho_f(c - 2));
+          const ff e3 = ff_sub_abs(rho_f(c + 3), rho_f(c - 3));
+          const ff D1 = ff_mul(ff_add_abs(ff_sub_abs(ff_mul_f(e1, 45.f), ff_mul_f(e2, 9.f)), e3), k1);
+          ff Ec = ff_add_abs(Ef[wrapi(c - 1, nx)], Ef[c]);
+          Ec.hi *= 0.5f;
+          Ec.lo *= 0.5f;
+          const ff J = ff_sub_abs(D1, ff_mul(Ec, C.rho[c]));
+          Df[c] = D1;
+          Jf[c] = J;
+          jsum = ff_add_abs(jsum, J);
         }
-        d1r *= inv_dx; d1J *= inv_dx; d2J *= r2; d3J *= r3;
-        const double Ec = 0.5 * (E_d(c - 1) + E_d(c));
-        const double rc = rho_d(c);
-        const double Rc = -d3J + Ec * d2J + (2.0 * rc - 3.0 * rb) * d1J + 2.0 * C.jd[c] * d1r -
-                          d1r * (C.jd[c] - meanJ);
-        const bool big_R = A.r_fac * fabs(Rc) > A.thr_R;
-        double nl = 0.0, nr = 0.0;
-        const G* pl = C.n2 + wrapi(c - 1, nx) * Lg;
-        const G* pr = C.n2 + c * Lg;
-        for (int q = 0; q < Lg; ++q) { nl += (double)pl[q]; nr += (double)pr[q]; }
-        nl = sqrt(nl); nr = sqrt(nr);
-        uint8_t s;
-        if (initial) {
-          s = (nl > A.thr_g || nr > A.thr_g || big_R) ? 1 : 0;
-          cell_cur[c] = s;
+        const float meanJ = block_sum_ff(jsum, red).hi * A.f_inv_nx;  // (syncs: Jc visible)
+        const float rbf = (float)rb;
+        for (int c = tid; c < nx; c += T) {
+          const ff J0 = Jf[c];
+          const ff Jm1 = Jf[wrapi(c - 1, nx)], Jp1 = Jf[wrapi(c + 1, nx)];
+          const ff Jm2 = Jf[wrapi(c - 2, nx)], Jp2 = Jf[wrapi(c + 2, nx)];
+          const ff Jm3 = Jf[wrapi(c - 3, nx)], Jp3 = Jf[wrapi(c + 3, nx)];
+          const ff e1 = ff_sub_abs(Jp1, Jm1), e2 = ff_sub_abs(Jp2, Jm2), e3 = ff_sub_abs(Jp3, Jm3);
+          const ff s1 = ff_add_abs(Jp1, Jm1), s2 = ff_add_abs(Jp2, Jm2), s3 = ff_add_abs(Jp3, Jm3);
+          const ff n3 = ff_sub_abs(ff_add_abs(ff_mul_f(e1, -13.f), ff_mul_f(e2, 8.f)), e3);
+          const ff n2 = ff_add_abs(ff_add_abs(ff_mul_f(s1, 270.f), ff_mul_f(s2, -27.f)),
+                                   ff_add_abs(ff_mul_f(s3, 2.f), ff_mul_f(J0, -490.f)));
+          const float d3J = n3.hi * A.f_k3;
+          const float d2J = n2.hi * A.f_k2;
+          const float d1J = (45.f * e1.hi - 9.f * e2.hi + e3.hi) * A.f_k1;
+          const float d1r = Df[c].hi, jc = J0.hi, rc = C.rho[c].hi;
+          const float Ec = 0.5f * (Ef[wrapi(c - 1, nx)].hi + Ef[c].hi);
+          const float Rc = -d3J + Ec * d2J + (2.f * rc - 3.f * rbf) * d1J + 2.f * jc * d1r - d1r * (jc - meanJ);
+          const bool big_R = A.f_rfac * fabsf(Rc) > A.f_thr_R;
+          const bool gl = C.n2[wrapi(c - 1, nx)] > A.f_thr_g2, gr = C.n2[c] > A.f_thr_g2;
+          uint8_t s;
+          if (initial) {
+            s = (gl || gr || big_R) ? 1 : 0;
+            cell_cur[c] = s;
+          }
+          const uint8_t cur = initial ? s : cell_cur[c];
+          if (!cur) s = big_R ? 1 : 0;
+          else s = (!gl && !gr && !big_R) ? 0 : 1;
+          cell_nxt[c] = s;
         }
-        const uint8_t cur = initial ? s : cell_cur[c];
-        if (!cur) s = big_R ? 1 : 0;
-        else s = (nl <= A.thr_g && nr <= A.thr_g && !big_R) ? 0 : 1;
-        cell_nxt[c] = s;
+      } else {
+        const double inv_dx = A.inv_dx;
+        auto rho_d = [&](int c) { return C.rd[wrapi(c, nx)]; };
+        auto E_d = [&](int c) { return C.ed[wrapi(c, nx)]; };
+        double jsum = 0.0;
+        for (int c = tid; c < nx; c += T) {
+          double d1 = 0.0;
+          for (int k = -3; k <= 3; ++k) d1 += kFD[0][k + 3] * rho_d(c + k);
+          d1 *= inv_dx;
+          const double Ec = 0.5 * (E_d(c - 1) + E_d(c));
+          C.jd[c] = d1 - Ec * rho_d(c);
+          jsum += C.jd[c];
+        }
+        const double meanJ = block_sum_d(jsum, red) / nx;  // (syncs: Jc visible)
+        const double r2 = 1.0 / (A.dx * A.dx), r3 = r2 / A.dx;
+        for (int c = tid; c < nx; c += T) {
+          double d1r = 0.0, d1J = 0.0, d2J = 0.0, d3J = 0.0;
+          for (int k = -3; k <= 3; ++k) {
+            const double jk = C.jd[wrapi(c + k, nx)];
+            d1r += kFD[0][k + 3] * rho_d(c + k);
+            d1J += kFD[0][k + 3] * jk;
+            d2J += kFD[1][k + 3] * jk;
+            d3J += kFD[2][k + 3] * jk;
+          }
+          d1r *= inv_dx; d1J *= inv_dx; d2J *= r2; d3J *= r3;
+          const double Ec = 0.5 * (E_d(c - 1) + E_d(c));
+          const double rc = rho_d(c);
+          const double Rc = -d3J + Ec * d2J + (2.0 * rc - 3.0 * rb) * d1J + 2.0 * C.jd[c] * d1r -
+                            d1r * (C.jd[c] - meanJ);
+          const bool big_R = A.r_fac * fabs(Rc) > A.thr_R;
+          const double nl = sqrt((double)C.n2[wrapi(c - 1, nx)]), nr = sqrt((double)C.n2[c]);
+          uint8_t s;
+          if (initial) {
+            s = (nl > A.thr_g || nr > A.thr_g || big_R) ? 1 : 0;
+            cell_cur[c] = s;
+          }
+          const uint8_t cur = initial ? s : cell_cur[c];
+          if (!cur) s = big_R ? 1 : 0;
+          else s = (nl <= A.thr_g && nr <= A.thr_g && !big_R) ? 0 : 1;
+          cell_nxt[c] = s;
+        }
       }
       __syncthreads();  // cell_cur of all cells visible
 
       // interface flags under s^n; an interface is written while it is
       // kinetic and for the two steps after it turns fluid, so that both
-      // step buffers hold its zeros
-      int nw = 0, nk = 0;
-      for (int c = c0; c < c1; ++c) {
-        const uint8_t k = cell_cur[c] | cell_cur[wrapi(c + 1, nx)];
-        kin_cur[c] = k;
-        nk += k;
-        nw += (k | kin_prev[c] | kin_prev2[c]) ? 1 : 0;
+      // step buffers hold its zeros.  Compaction of the interfaces to write,
+      // in increasing order: rows of T cells (cell k T + tid), one ballot
+      // per warp and row, an exclusive scan of the per-(row, warp) counts,
+      // then each flagged cell's slot from the popcount of the lanes below
+      // it.
+      constexpr int NW = T / 32;
+      const int nrow = (nx + T - 1) / T;
+      int* cnt = reinterpret_cast<int*>(C.base);  // [nrow][NW]
+      int nk = 0;
+      for (int k = 0; k < nrow; ++k) {
+        const int c = k * T + tid;
+        bool wr = false;
+        if (c < nx) {
+          const uint8_t kf = cell_cur[c] | cell_cur[wrapi(c + 1, nx)];
+          kin_cur[c] = kf;
+          nk += kf;
+          wr = (kf | kin_prev[c] | kin_prev2[c]) != 0;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, wr);
+        if (l == 0) cnt[k * NW + w] = __popc(b);
       }
-      int tot_w, tot_k;
-      int pos0 = block_scan2_i(nw, nk, ired, &tot_w, &tot_k);
-      for (int c = c0; c < c1; ++c)
-        if (kin_cur[c] | kin_prev[c] | kin_prev2[c]) C.list[pos0++] = c;
-      count = tot_w;
-      if (tid == 0) kin_total += tot_k;
+      nk = __reduce_add_sync(0xffffffffu, nk);
+      if (l == 0) atomicAdd(&rint[1], nk);
+      __syncthreads();
+      if (w == 0) {
+        const int ne = nrow * NW, per = (ne + 31) / 32;
+        const int q0 = min(l * per, ne), q1 = min(q0 + per, ne);
+        int sum = 0;
+        for (int q = q0; q < q1; ++q) sum += cnt[q];
+        int inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, inc, d);
+          if (l >= d) inc += t;
+        }
+        int run = inc - sum;
+        for (int q = q0; q < q1; ++q) {
+          const int v = cnt[q];
+          cnt[q] = run;
+          run += v;
+        }
+        if (l == 31) rint[0] = inc;
+      }
+      __syncthreads();
+      count = rint[0];
+      for (int k = 0; k < nrow; ++k) {
+        const int c = k * T + tid;
+        const bool wr = c < nx && (kin_cur[c] | kin_prev[c] | kin_prev2[c]);
+        const unsigned b = __ballot_sync(0xffffffffu, wr);
+        if (wr) C.list[cnt[k * NW + w] + __popc(b & ((1u << l) - 1u))] = c;
+      }
     } else {
       count = nx;
       if (tid == 0) kin_total += nx;
     }
 
     // J and the sweep constants: E+/dv, E-/dv, P = <X>, J
-    for (int c = c0; c < c1; ++c) {
+    for (int c = tid; c < nx; c += T) {
       const int cl = wrapi(c - 1, nx), cr = wrapi(c + 1, nx);
       G* pr = C.par + 4 * c;
       const G e = pr[3];
       const G J = M::flux_J(C.rho[c], C.rho[cr], e, g_inv_dx);
-      C.jg[c] = J;
       const G ep = e > G(0) ? e : G(0), em = e < G(0) ? -e : G(0);
-      const G pm = ((C.mp[c] - C.mp[cl]) - (C.mm[cr] - C.mm[c])) * g_inv_dx;
+      const G pm = ((mplus(c) - mplus(cl)) - (mminus(cr) - mminus(c))) * g_inv_dx;
       const G* en = C.ends + 4 * c;
       const G gend = (G)0.5 * ((ep * en[2] - em * en[3]) - (ep * en[0] - em * en[1]));
       pr[0] = ep * g_inv_dv;
@@ -614,6 +804,9 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       pr[3] = J;
     }
     __syncthreads();
+    if constexpr (ADAPT) {
+      if (tid == 0) kin_total += rint[1];
+    }
   };
 
   // ------------------------------------------------------------ macro C --
@@ -621,38 +814,42 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   // (kinetic: dt/dx <xi g>/eps, fluid: dt/dx (-m2 J)), or the cell-based
   // rule of S^HMM when flux_rule == 1.
   auto flux_kin = [&](int c) {
-    Acc s = M::azero();
-    const G* pp = C.part + c * Lg;
-    for (int q = 0; q < Lg; ++q) s = M::aadd(s, pp[q]);
-    return (G)M::aval(s, g_kflux);
+    const G* pr = C.part + 4 * c;
+    if constexpr (sizeof(G) == 4) {  // compensated: (pos + neg) + (errors)
+      const ff t = two_sum(pr[0], pr[2]);
+      const float e = __fadd_rn(__fadd_rn(pr[1], pr[3]), t.lo);
+      return __fmaf_rn(t.hi, g_kflux, __fmul_rn(e, g_kflux));
+    } else {
+      return (pr[0] + pr[2]) * g_kflux;
+    }
   };
   auto is_kin = [&](int c) { return ADAPT ? kin_cur[c] != 0 : true; };
+  // J of an interface: slot 3 of its sweep constants
+  auto Jat = [&](int c) { return C.par[4 * c + 3]; };
   auto macro_C = [&]() {
-    if (c0 < c1) {
-      if (A.flux_rule == 0) {
-        const int cl = wrapi(c0 - 1, nx);
-        G Fp = is_kin(cl) ? flux_kin(cl) : g_fflux * C.jg[cl];
-        for (int c = c0; c < c1; ++c) {
-          const G Fc = is_kin(c) ? flux_kin(c) : g_fflux * C.jg[c];
-          C.rho[c] = M::addg(M::addg(C.rho[c], Fp), -Fc);
-          Fp = Fc;
+    if (A.flux_rule == 0) {
+      // each interface flux is evaluated by both of its cells, from the same
+      // inputs, so the two evaluations are bitwise equal and mass telescopes
+      for (int c = tid; c < nx; c += T) {
+        const int cl = wrapi(c - 1, nx);
+        const G Fl = is_kin(cl) ? flux_kin(cl) : g_fflux * Jat(cl);
+        const G Fc = is_kin(c) ? flux_kin(c) : g_fflux * Jat(c);
+        C.rho[c] = M::addg(M::addg(C.rho[c], Fl), -Fc);
+      }
+    } else {
+      for (int c = tid; c < nx; c += T) {
+        const int cl = wrapi(c - 1, nx);
+        G Fr, Fl;
+        if (!ADAPT || cell_cur[c]) {
+          Fr = is_kin(c) ? flux_kin(c) : G(0);
+          Fl = is_kin(cl) ? flux_kin(cl) : G(0);
+        } else {
+          Fr = g_fflux * Jat(c);
+          Fl = g_fflux * Jat(cl);
         }
-      } else {
-        for (int c = c0; c < c1; ++c) {
-          const int cl = wrapi(c - 1, nx);
-          G Fr, Fl;
-          if (!ADAPT || cell_cur[c]) {
-            Fr = is_kin(c) ? flux_kin(c) : G(0);
-            Fl = is_kin(cl) ? flux_kin(cl) : G(0);
-          } else {
-            Fr = g_fflux * C.jg[c];
-            Fl = g_fflux * C.jg[cl];
-          }
-          C.rho[c] = M::addg(M::addg(C.rho[c], Fl), -Fr);
-        }
+        C.rho[c] = M::addg(M::addg(C.rho[c], Fl), -Fr);
       }
     }
-    for (int c = c0; c < c1; ++c) moments(c);
   };
 
   // --------------------------------------------------------------- sweep --
@@ -679,10 +876,10 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       last = i;
       const G left_nb = __shfl_sync(0xffffffffu, Cc[VPT - 1], src_left);
       const G right_nb = __shfl_sync(0xffffffffu, Cc[0], src_right);
+      G psum = 0, nsum = 0;
       if (valid) {
         const bool kin = ADAPT ? (kin_cur[i] != 0) : true;
         G out[VPT];
-        G psum = 0, nsum = 0;
         if (kin) {
           const float4* pr4 = reinterpret_cast<const float4*>(C.par + 4 * i);
           G Ep, Em, Pp, Jv;
@@ -718,8 +915,6 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           vstore<G, VPT>(dst + (unsigned)(i * nv + j0), out);
           if (valid) vload<G, VPT>(P, col(i + 3));
         }
-        C.part[i * Lg + lig] = psum;
-        if constexpr (ADAPT) C.n2[i * Lg + lig] = nsum;
         if constexpr (VPT >= 2) {
           if (first_lane) { C.ends[4 * i + 0] = out[0]; C.ends[4 * i + 1] = out[1]; }
           if (last_lane) { C.ends[4 * i + 2] = out[VPT - 2]; C.ends[4 * i + 3] = out[VPT - 1]; }
@@ -727,6 +922,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           if (end_slot >= 0) C.ends[4 * i + end_slot] = out[0];
         }
       }
+      reduce_store(i, valid, psum, nsum);
     };
     for (int e = e0; e < e0 + epg; e += 4) {
       body(e + 0, R0, R1, R2, R3);
@@ -755,7 +951,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
 
   // ---- epilogue
   int bad = 0;
-  for (int c = c0; c < c1; ++c) {
+  for (int c = tid; c < nx; c += T) {
     const double r = M::tod(C.rho[c]);
     rout[c] = r;
     if (!isfinite(r)) bad = 1;
@@ -766,17 +962,17 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
 }
 
 // One CTA per state of a uniform batch.
-template <class G, int VPT, bool ADAPT, bool CSMEM>
+template <class G, int VPT, bool ADAPT>
 __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t st = blockIdx.x;
   const size_t sz = (size_t)A.nx * A.nv;
-  unsigned char* colbase = CSMEM ? smem + 8 * kRedSlots
-                                 : reinterpret_cast<unsigned char*>(A.col_ws) + st * A.col_ws_stride;
-  fine_state<G, VPT, ADAPT, CSMEM>(A, A.rho_in + st * A.nx, reinterpret_cast<const G*>(A.g_in) + st * sz,
-                                   reinterpret_cast<G*>(A.g_buf0) + st * sz,
-                                   reinterpret_cast<G*>(A.g_buf1) + st * sz, A.rho_out + st * A.nx,
-                                   A.mask_out ? A.mask_out + st * A.nx : nullptr, smem, colbase);
+  unsigned char* colglob =
+      A.col_ws ? reinterpret_cast<unsigned char*>(A.col_ws) + st * A.col_ws_stride : nullptr;
+  fine_state<G, VPT, ADAPT>(A, A.rho_in + st * A.nx, reinterpret_cast<const G*>(A.g_in) + st * sz,
+                            reinterpret_cast<G*>(A.g_buf0) + st * sz, reinterpret_cast<G*>(A.g_buf1) + st * sz,
+                            A.rho_out + st * A.nx, A.mask_out ? A.mask_out + st * A.nx : nullptr, smem,
+                            smem + 8 * kRedSlots, colglob, kColBudgetFine);
 }
 
 // Persistent work-list kernel: each CTA takes (solve, slice) items from a
@@ -784,19 +980,19 @@ __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A)
 // fine propagations; the list is sorted by decreasing cost on the host).
 // An item propagates rho^{n,k} of its solve (g from slice 0's data, or
 // lifted from the density) and writes F(rho)^{n+1}.  The step buffers and
-// (when they do not fit shared memory) the column arrays are per-CTA
-// workspace reused from item to item.
-template <class G, int VPT, bool ADAPT, bool CSMEM>
+// the column arrays that do not fit shared memory are per-CTA workspace
+// reused from item to item.
+template <class G, int VPT, bool ADAPT>
 __global__ void __launch_bounds__(kFineThreads, 1)
     fine_list_kernel(const FineListSolve* solves, const FineListItem* items, int n_items, int* next,
                      unsigned char* ws, size_t ws_g, size_t ws_col) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ __align__(16) FineArgs s_args;
-  unsigned char* mine = ws + (size_t)blockIdx.x * (2 * ws_g + (CSMEM ? 0 : ws_col));
+  unsigned char* mine = ws + (size_t)blockIdx.x * (2 * ws_g + ws_col);
   G* b0 = reinterpret_cast<G*>(mine);
   G* b1 = reinterpret_cast<G*>(mine + ws_g);
-  unsigned char* colbase = CSMEM ? smem + 8 * kRedSlots : mine + 2 * ws_g;
+  unsigned char* colglob = ws_col ? mine + 2 * ws_g : nullptr;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
     __syncthreads();
@@ -812,61 +1008,50 @@ __global__ void __launch_bounds__(kFineThreads, 1)
     __syncthreads();
     const int nx = s_args.nx;
     const G* gin = (it.slice == 0 && S->g0) ? reinterpret_cast<const G*>(S->g0) : nullptr;
-    fine_state<G, VPT, ADAPT, CSMEM>(s_args, S->rho + (size_t)it.slice * nx, gin, b0, b1,
-                                     S->frho + (size_t)(it.slice + 1) * nx, nullptr, smem, colbase);
+    fine_state<G, VPT, ADAPT>(s_args, S->rho + (size_t)it.slice * nx, gin, b0, b1,
+                              S->frho + (size_t)(it.slice + 1) * nx, nullptr, smem, smem + 8 * kRedSlots,
+                              colglob, kColBudgetList);
     __syncthreads();  // before the next item overwrites s_args, s_item and the buffers
   }
 }
 
 // ---------------------------------------------------------------- launch --
 
-template <class G, int VPT, bool ADAPT, bool CSMEM>
+template <class G, int VPT, bool ADAPT>
 static cudaError_t launch_t(const FineArgs& a, size_t smem, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fine_kernel<G, VPT, ADAPT, CSMEM>,
+    cudaError_t e = cudaFuncSetAttribute(fine_kernel<G, VPT, ADAPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fine_kernel<G, VPT, ADAPT, CSMEM><<<a.batch, kFineThreads, smem, s>>>(a);
+  fine_kernel<G, VPT, ADAPT><<<a.batch, kFineThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <class G, int VPT>
 static cudaError_t launch_v(const FineArgs& a, size_t smem, cudaStream_t s) {
-  if (a.adapt) {
-    return a.col_in_smem ? launch_t<G, VPT, true, true>(a, smem, s) : launch_t<G, VPT, true, false>(a, smem, s);
-  }
-  return a.col_in_smem ? launch_t<G, VPT, false, true>(a, smem, s) : launch_t<G, VPT, false, false>(a, smem, s);
+  return a.adapt ? launch_t<G, VPT, true>(a, smem, s) : launch_t<G, VPT, false>(a, smem, s);
 }
 
-template <class G, int VPT, bool ADAPT, bool CSMEM>
+template <class G, int VPT, bool ADAPT>
 static cudaError_t launch_list_t(const FineList& L, size_t smem, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fine_list_kernel<G, VPT, ADAPT, CSMEM>,
+    cudaError_t e = cudaFuncSetAttribute(fine_list_kernel<G, VPT, ADAPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fine_list_kernel<G, VPT, ADAPT, CSMEM><<<L.grid, kFineThreads, smem, s>>>(L.solves, L.items, L.n_items, L.next,
-                                                                            L.ws, L.ws_g, L.ws_col);
+  fine_list_kernel<G, VPT, ADAPT><<<L.grid, kFineThreads, smem, s>>>(L.solves, L.items, L.n_items, L.next,
+                                                                     L.ws, L.ws_g, L.ws_col);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, bool col_in_smem, size_t smem,
-                             cudaStream_t s) {
-  if (fp32) {
-    if (adapt) return col_in_smem ? launch_list_t<float, 8, true, true>(L, smem, s)
-                                  : launch_list_t<float, 8, true, false>(L, smem, s);
-    return col_in_smem ? launch_list_t<float, 8, false, true>(L, smem, s)
-                       : launch_list_t<float, 8, false, false>(L, smem, s);
-  }
-  if (adapt) return col_in_smem ? launch_list_t<double, 4, true, true>(L, smem, s)
-                                : launch_list_t<double, 4, true, false>(L, smem, s);
-  return col_in_smem ? launch_list_t<double, 4, false, true>(L, smem, s)
-                     : launch_list_t<double, 4, false, false>(L, smem, s);
+cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, size_t smem, cudaStream_t s) {
+  if (fp32) return adapt ? launch_list_t<float, 8, true>(L, smem, s) : launch_list_t<float, 8, false>(L, smem, s);
+  return adapt ? launch_list_t<double, 4, true>(L, smem, s) : launch_list_t<double, 4, false>(L, smem, s);
 }
 
 cudaError_t launch_fine(const FineArgs& args, int vpt, bool fp32, size_t smem, cudaStream_t s) {

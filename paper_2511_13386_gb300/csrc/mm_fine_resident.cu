@@ -537,6 +537,20 @@ int fine_resident_cluster(int nx, int nv, bool fp32, bool adapt, int flux_rule, 
   return 0;
 }
 
+// Shared-memory bytes of the resident kernel with clusters of C CTAs, or 0
+// when that cluster size does not suit the shape (same rules as above, for
+// the autotuner).
+size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, int C) {
+  if (!fp32 || adapt || flux_rule != 0 || nv % VPT) return 0;
+  const int lanes = nv / VPT;
+  if (lanes < 2 || lanes > 32 || (lanes & (lanes - 1))) return 0;
+  if (C < 1 || C > 8 || (C & (C - 1)) || nx % C) return 0;
+  const int n = nx / C;
+  if (n % 32 || n > T || n % (T / lanes) || (n / (T / lanes)) % 4) return 0;
+  const unsigned bytes = res_map(n, nv, lanes, C).total;
+  return bytes <= 232448u ? bytes : 0;
+}
+
 template <int LG>
 static cudaError_t launch_res(const FineArgs& a, int C, size_t smem, cudaStream_t s) {
   static bool configured = false;

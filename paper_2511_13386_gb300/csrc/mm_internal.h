@@ -17,7 +17,7 @@ constexpr int kVTabFields = 6;      // per velocity node: |v|/dx, M, v M, w v, w
 // Velocity constants of one context, built on the host in double.
 struct VelocityGrid {
   int nv = 0;
-  double dv = 0, m2 = 0, xiM = 0;
+  double dv = 0, m2 = 0, xiM = 0, mu3 = 0;  // m2 = <v^2 M>, xiM = <v M>, mu3 = <v^3 M>
   std::vector<double> v, w, M;
 };
 
@@ -55,7 +55,13 @@ struct FineArgs {
   // instruction is needed (or re-issued) inside the FP32 kernels' step loop
   float fa, fb, f_dx, f_inv_dx, f_inv_dv, f_kflux, f_fflux, f_inv_nx;
   float f_dx_lo, f_inv_nx_lo;  // low parts of dx and 1/nx as float-float
+  // adaptation criteria of the FP32 path: 1/(60 dx) as float-float (first
+  // derivative stencil of Table 1 with integer weights), 1/(180 dx^2),
+  // 1/(8 dx^3), thr_g^2, thr_R, r_fac
+  float f_k1, f_k1_lo, f_k2, f_k3, f_thr_g2, f_thr_R, f_rfac;
   double xiM;                  // <xi M> of the discrete Maxwellian (lifting)
+  double mu3;                  // <xi^3 M> (lifting of order three)
+  int lift_order;              // order L of the lifting (Def. 1), 1..3
 };
 
 // Work list of fine propagations across solves (persistent kernel).
@@ -78,8 +84,7 @@ struct FineList {
 };
 // Launch the persistent list kernel: FP32 (8 nodes per lane) or FP64 (4);
 // every solve of the list must share precision and adaptation.
-cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, bool col_in_smem, size_t smem,
-                             cudaStream_t s);
+cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, size_t smem, cudaStream_t s);
 
 // Fill the float copies of a FineArgs from its double fields.
 inline void fine_args_floats(FineArgs& a) {
@@ -93,11 +98,21 @@ inline void fine_args_floats(FineArgs& a) {
   a.f_fflux = (float)(-a.dt_dx * a.m2);
   a.f_inv_nx = (float)(1.0 / a.nx);
   a.f_inv_nx_lo = (float)(1.0 / a.nx - (double)a.f_inv_nx);
+  const double k1 = a.inv_dx / 60.0;
+  a.f_k1 = (float)k1;
+  a.f_k1_lo = (float)(k1 - (double)a.f_k1);
+  a.f_k2 = (float)(a.inv_dx * a.inv_dx / 180.0);
+  a.f_k3 = (float)(a.inv_dx * a.inv_dx * a.inv_dx / 8.0);
+  a.f_thr_g2 = (float)(a.thr_g * a.thr_g);
+  a.f_thr_R = (float)a.thr_R;
+  a.f_rfac = (float)a.r_fac;
 }
 
-// Column-array footprint of one state (bytes), for the chosen precision.
-size_t fine_column_bytes(int nx, int nv, int lanes, bool fp32, bool adapt);
-size_t fine_smem_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool col_in_smem);
+// Column arrays of one state: the bytes that go to global memory (0 when
+// all of them fit shared memory) and the kernel's dynamic shared memory,
+// for the fine kernel (list = false) or the work-list kernel (list = true).
+size_t fine_column_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool list);
+size_t fine_smem_bytes(int nx, int nv, int lanes, bool fp32, bool adapt, bool list);
 
 // Launch the fine kernel for a batch (one CTA per state).
 cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem,
@@ -107,12 +122,14 @@ cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem,
 // one thread-block cluster per state).  fine_resident_cluster returns the
 // cluster size (0: shape not supported) and the dynamic shared memory.
 int fine_resident_cluster(int nx, int nv, bool fp32, bool adapt, int flux_rule, size_t* smem);
+size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, int C);
 cudaError_t launch_fine_resident(const FineArgs& a, int C, size_t smem, cudaStream_t s);
 
 // Arguments of the macroscopic kernels (coarse step, lift, correction).
 struct MacroArgs {
   int nx, nv, batch;
-  double dx, inv_dx, m2, rho_bar, eps, xiM;
+  double dx, inv_dx, m2, rho_bar, eps, xiM, mu3;
+  int lift_order;       // order L of the lifting (Def. 1), 1..3
   int coarse_kind, coarse_steps;
   int parts;            // chunks of the partitioned tridiagonal solve
   double t_span;

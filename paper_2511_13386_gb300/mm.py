@@ -27,7 +27,7 @@ STATUS_NAMES = ["MM_OK", "MM_ERR_INVALID", "MM_ERR_OOM", "MM_ERR_CUDA", "MM_ERR_
                 "MM_ERR_UNSTABLE", "MM_ERR_BUSY", "MM_ERR_NOT_READY", "MM_ERR_UNKNOWN_TICKET"]
 
 EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine_propagate",
-            "mm_fine_propagate_noalloc", "mm_coarse", "mm_lift", "parareal_run", "mm_batch_footprint",
+            "mm_fine_propagate_noalloc", "mm_autotune", "mm_coarse", "mm_lift", "parareal_run", "mm_batch_footprint",
             "mm_batch_create", "mm_batch_add", "mm_batch_step", "mm_batch_query", "mm_batch_take",
             "mm_batch_bytes", "mm_batch_counters", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
             "serve_poll", "mm_server_destroy", "mm_last_error"]
@@ -46,7 +46,8 @@ class mm_params(ctypes.Structure):
                 ("r_scale", ctypes.c_int32), ("flux_rule", ctypes.c_int32), ("dt", ctypes.c_double),
                 ("cfl_theta", ctypes.c_double), ("coarse_kind", ctypes.c_int32),
                 ("coarse_steps", ctypes.c_int32), ("lift_order", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("fine_kernel", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("fine_kernel", ctypes.c_int32),
+                ("fine_vpt", ctypes.c_int32)]
 
 
 class mm_alloc(ctypes.Structure):
@@ -64,6 +65,14 @@ class mm_fine_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("kinetic_updates", ctypes.c_int64),
                 ("full_updates", ctypes.c_int64), ("device_status", ctypes.c_int32),
                 ("elapsed_ms", ctypes.c_double)]
+
+
+class mm_tune_result(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("fine_kernel", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("vpt", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("cand_kernel", ctypes.c_int32 * 16),
+                ("cand_cluster", ctypes.c_int32 * 16), ("cand_vpt", ctypes.c_int32 * 16),
+                ("cand_ms", ctypes.c_double * 16)]
 
 
 class mm_parareal_cfg(ctypes.Structure):
@@ -118,6 +127,7 @@ def load(build_if_missing: bool = True):
                                                  P(mm_fine_stats), V]),
             "mm_fine_propagate_noalloc": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V,
                                                          V, V, P(mm_fine_stats), V]),
+            "mm_autotune": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_int32, V, V, V, V, P(mm_tune_result), V]),
             "mm_coarse": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V]),
             "mm_lift": (ctypes.c_int, [V, ctypes.c_int32, V, V, V]),
             "parareal_run": (ctypes.c_int, [V, P(mm_parareal_cfg), V, V, V, P(mm_parareal_stats), V]),
@@ -241,6 +251,20 @@ def mm_fine_propagate_noalloc(ctx: Ctx, batch: int, t_span: float, rho_in, g_in,
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def mm_autotune(ctx: Ctx, batch: int, steps: int, rho_in, g_in, rho_out, g_out, stream=None) -> dict:
+    """Pick F's fastest launch shape for this context by timing every
+    candidate on the given batch (outputs are scratch); batch == 0 restores
+    the default.  Returns the choice and the candidates' times."""
+    r = mm_tune_result()
+    _check(load().mm_autotune(ctx.handle, batch, steps, _ptr(rho_in), _ptr(g_in), _ptr(rho_out),
+                              _ptr(g_out), ctypes.byref(r), _stream(stream)))
+    n = min(r.n_candidates, 16)
+    return {"n_candidates": r.n_candidates, "fine_kernel": r.fine_kernel, "cluster": r.cluster,
+            "vpt": r.vpt, "lanes": r.lanes, "best_ms": r.best_ms,
+            "candidates": [{"fine_kernel": r.cand_kernel[q], "cluster": r.cand_cluster[q],
+                            "vpt": r.cand_vpt[q], "ms": r.cand_ms[q]} for q in range(n)]}
 
 
 def mm_coarse(ctx: Ctx, batch: int, t_span: float, rho_in, rho_out, stream=None):

@@ -113,3 +113,38 @@ def test_parareal_hybrid(prec):
     ref, err, it = O.parareal(oparams(p), w.rho0, w.g0, w.t_end, w.n_slices, 2)
     tol = FP64_TOL if prec == mm.MM_FP64 else FP32_TOL
     assert rel(out, ref) <= tol, rel(out, ref)
+
+
+@pytest.mark.parametrize("eps,L", [(1.0, 1), (1e-1, 3), (1e-3, 3)])
+def test_parareal_paper_setup(eps, L):
+    """The paper's own setup (Sec. 5) in its 1D-1V reduction: torus length
+    2 pi, f = M v^4 (1 + 0.9 cos x), thresholds 1e-5 on both criteria,
+    lifting of order 3 (order 1 at eps = 1, where the truncated
+    Chapman-Enskog series of order 3 makes the relifted iteration diverge
+    on this data, eps k = 1); here N = 8 slices over T = 0.2 and K = 3,
+    FP64, against the oracle's Algorithm 1 with the same options."""
+    dev = device()
+    w = W.paper(eps, n_slices=8)
+    w.t_end = 0.2
+    p = params(w.nx, w.nv, eps, mm.MM_FP64, v_max=w.v_max, x_len=w.x_len, rho_bar=w.rho_bar,
+               adapt=1, thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, lift_order=L)
+    ctx = mm.mm_create(p)
+    out = torch.empty((w.n_slices + 1, w.nx), dtype=torch.float64, device=dev)
+    info = mm.parareal_run(ctx, w.t_end, w.n_slices, 3, 0.0, torch.tensor(w.rho0, device=dev),
+                           torch.tensor(w.g0, device=dev), out)
+    ctx.close()
+    op = oparams(p)
+    ref, err, it = O.parareal(op, w.rho0, w.g0, w.t_end, w.n_slices, 3, lift_order=L)
+    assert info["iterations"] == it == 3
+    got = out.cpu().numpy()
+    # slice 1 is one fine propagation of the given data: 1e-12; later slices
+    # within the oracle's own sensitivity to one-ulp changes of rho0
+    assert rel(got[:2], ref[:2]) <= FP64_TOL, rel(got[:2], ref[:2])
+    rng = np.random.default_rng(3)
+    sens = 0.0
+    for _ in range(2):
+        r0 = w.rho0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=w.nx))
+        o2, _, _ = O.parareal(op, r0, w.g0, w.t_end, w.n_slices, 3, lift_order=L)
+        sens = max(sens, rel(o2, ref))
+    assert rel(got, ref) <= max(FP64_TOL, 20 * sens), (rel(got, ref), sens)
+    assert info["mass_drift"] <= 1e-12
