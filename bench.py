@@ -542,8 +542,8 @@ def run_paper(a):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (the paper's initial condition)",
             "config": {"workload": "paper setup, 1D-1V reduction: Nx=32, Nv=32 on [-8,8], x_len=2pi, "
-                                   "f = M v^4 (1 + 0.9 cos x), T=1, N=200, tol 1e-10, thresholds 1e-5, lift order 3 "
-                                   "(1 at eps >= 0.5)"},
+                                   "f = M v^4 (1 + 0.9 cos x), T=1, N=200, tol 1e-10, thresholds 1e-5 on ||g|| and "
+                                   "eps^2 |R|, lift order 3 (1 at eps >= 0.5)"},
             "matrix": rows}
     print(json.dumps(line))
 
