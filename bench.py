@@ -406,6 +406,9 @@ def run_hybrid(a):
     mask = torch.empty(rho.shape, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    # launch shape picked by the autotuner on these states over the window
+    tune = mm.mm_autotune(ctx, a.states, window, rho, g, ro, go)
+    q = mm.mm_query(ctx, span)
     for _ in range(a.warmup):
         st = mm.mm_fine_propagate(ctx, a.states, span, rho, g, ro, go, mask, stats=True)
     torch.cuda.synchronize()
@@ -444,6 +447,8 @@ def run_hybrid(a):
     launch_ms = statistics.mean(kin_ms)
     achieved = BYTES_PER_UPDATE * (upd / a.steps) / (launch_ms / 1e3) / 1e9
     kname = f"fine_kernel<float,{q['vpt']},adapt>"
+    autotune = {"chosen": kname, f"candidates_ms_{window}_steps": {
+        f"streaming {c['vpt']} nodes/lane": round(c["ms"], 3) for c in tune["candidates"]}}
     line = {"metric": "cell-updates/s", "value": upd / (total_ms / 1e3), "unit": "cell-updates/s", "n_gpus": 1,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -454,7 +459,8 @@ def run_hybrid(a):
                        "kinetic_update_fraction": round(kin_frac, 4),
                        "kinetic_cells_at_end": round(kinetic_cells, 4),
                        "l2": "flushed (256 MB write) before every timed step, outside the events; "
-                             "g is 512 MiB per buffer"},
+                             "g is 512 MiB per buffer",
+                       "autotune": autotune},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4), "traffic": profiled_traffic("streaming"),
                          "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",

@@ -92,7 +92,7 @@ typedef struct {
 
 /* Problem description.  Fill with mm_params_default() then override. */
 typedef struct {
-  int32_t nx;          /* cells, >= 8 */
+  int32_t nx;          /* cells, 8 <= nx <= 65536 */
   int32_t nv;          /* velocity nodes: even, >= 4, see mm_params_default */
   double x_len;        /* torus length (> 0) */
   double v_max;        /* velocity box half-width (> 0) */

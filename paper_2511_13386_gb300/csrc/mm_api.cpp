@@ -252,7 +252,7 @@ static bool choose_layout(int nv, bool fp32, mmk::LaneLayout* out) {
 
 static mm_status validate(const mm_params* p) {
   if (!p) return mm_fail(MM_ERR_INVALID, "params is NULL");
-  if (p->nx < 8) return mm_fail(MM_ERR_INVALID, "nx must be >= 8");
+  if (p->nx < 8 || p->nx > 65536) return mm_fail(MM_ERR_INVALID, "nx must be in [8, 65536]");
   if (p->nv < 4 || p->nv % 2) return mm_fail(MM_ERR_INVALID, "nv must be even and >= 4");
   if (!(p->x_len > 0) || !(p->v_max > 0) || !(p->eps > 0))
     return mm_fail(MM_ERR_INVALID, "x_len, v_max and eps must be positive");

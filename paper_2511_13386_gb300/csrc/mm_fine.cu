@@ -117,18 +117,23 @@ struct MP<float> {
 enum ColField {
   F_BASE,   // R [kFineThreads]: per-thread prefix bases of the Poisson law;
             //   then int [rows][warps] counts / offsets of the compaction
-  F_PAR,    // G [nx][4]: E+/dv, E-/dv, P = <X>, J per interface (sweep constants)
-  F_LIST,   // int [nx]: interfaces the sweep writes (adaptation)
+  F_PAR,    // G [nx][4]: E (value and low part), P = <X>, J per interface:
+            //   the sweep constants, and the field of the criteria; while the
+            //   criteria run, slot 2 (P of the last step, dead until the new
+            //   constants) holds the density derivative (FP32) or a copy of
+            //   the density (FP64)
   F_KIN0, F_KIN1, F_KIN2, F_CELL0, F_CELL1,  // uint8 [nx] status flags (adaptation)
   F_RHO,    // R [nx]: density (float-float or double)
-  F_JD,     // 8 B [nx]: centred flux of the criteria (adaptation)
-  F_ED,     // 8 B [nx]: field of the criteria (adaptation)
-  F_PART,   // G [nx][4]: sums of w v g over the negative / positive velocities
-            //   (value and compensation each), one record per interface
+  F_FK,     // G [nx]: kinetic interface flux dt/dx <xi g>/eps of the last sweep
+  F_MP,     // G [nx]: m+ = <v^+ g> of the last sweep
+  F_MM,     // G [nx]: m- = <v^- g> of the last sweep
   F_N2,     // G [nx]: <g^2> per interface (adaptation)
+  F_JD,     // 8 B [nx]: centred flux of the criteria (adaptation); with
+            //   adaptation the Poisson prefix sums (first half of the macro
+            //   phase) and the write list (compaction to the end of the
+            //   sweep) share it: the three lifetimes are disjoint
   F_ENDS,   // G [nx][4]: g at the two lowest and the two highest nodes
-  F_RD,     // 8 B [nx]: first derivative of the density (adaptation)
-  F_S,      // R [nx]: prefix sums of the Poisson law
+  F_S,      // R [nx]: prefix sums of the Poisson law (without adaptation)
   F_COUNT
 };
 
@@ -155,16 +160,15 @@ __host__ __device__ inline ColLayout col_layout(int nx, int gbytes, bool adapt, 
   sz[F_BASE] = 8 * (size_t)kFineThreads > 4 * rows * (kFineThreads / 32) ? 8 * (size_t)kFineThreads
                                                                           : 4 * rows * (kFineThreads / 32);
   sz[F_PAR] = gbytes * 4 * n;
-  sz[F_LIST] = a * 4 * n;
   sz[F_KIN0] = sz[F_KIN1] = sz[F_KIN2] = sz[F_CELL0] = sz[F_CELL1] = a * n;
   sz[F_RHO] = 8 * n;
-  sz[F_JD] = a * 8 * n;
-  sz[F_ED] = a * 8 * n;
-  sz[F_PART] = gbytes * 4 * n;
+  sz[F_FK] = gbytes * n;
+  sz[F_MP] = gbytes * n;
+  sz[F_MM] = gbytes * n;
   sz[F_N2] = a * gbytes * n;
+  sz[F_JD] = a * 8 * n;
   sz[F_ENDS] = gbytes * 4 * n;
-  sz[F_RD] = a * 8 * n;
-  sz[F_S] = 8 * n;
+  sz[F_S] = (1 - a) * 8 * n;
   ColLayout L;
   L.smem_mask = 0;
   L.smem_total = 0;
@@ -285,9 +289,9 @@ template <class G>
 struct Cols {
   using R = typename MP<G>::R;
   R *rho, *S, *base;
-  G *part, *n2, *ends, *par;
-  int* list;
-  double *ed, *rd, *jd;
+  G *fk, *mp, *mm, *n2, *ends, *par;
+  uint16_t* list;
+  double* jd;
   uint8_t *cell0, *cell1, *kin0, *kin1, *kin2;
 };
 
@@ -299,15 +303,15 @@ __device__ __forceinline__ Cols<G> carve(unsigned char* sbase, unsigned char* gb
   auto at = [&](int f) { return ((L.smem_mask >> f) & 1u ? sbase : gbase) + L.off[f]; };
   Cols<G> c;
   c.rho = reinterpret_cast<R*>(at(F_RHO));
-  c.S = reinterpret_cast<R*>(at(F_S));
+  c.S = reinterpret_cast<R*>(at(adapt ? F_JD : F_S));
   c.base = reinterpret_cast<R*>(at(F_BASE));
-  c.part = reinterpret_cast<G*>(at(F_PART));
+  c.fk = reinterpret_cast<G*>(at(F_FK));
+  c.mp = reinterpret_cast<G*>(at(F_MP));
+  c.mm = reinterpret_cast<G*>(at(F_MM));
   c.n2 = reinterpret_cast<G*>(at(F_N2));
   c.ends = reinterpret_cast<G*>(at(F_ENDS));
   c.par = reinterpret_cast<G*>(at(F_PAR));
-  c.list = reinterpret_cast<int*>(at(F_LIST));
-  c.ed = reinterpret_cast<double*>(at(F_ED));
-  c.rd = reinterpret_cast<double*>(at(F_RD));
+  c.list = reinterpret_cast<uint16_t*>(at(F_JD));
   c.jd = reinterpret_cast<double*>(at(F_JD));
   c.cell0 = at(F_CELL0);
   c.cell1 = at(F_CELL1);
@@ -410,11 +414,11 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   Cols<G> C = carve<G>(colsmem, colglob, nx, ADAPT, budget);
   if (gin == nullptr) {  // the lifted density goes where the first step does not write
     G* lifted = (A.n_steps & 1) ? buf1 : buf0;
-    // E and J of the lifting use the sweep-constant array, K, dK and dtJ
-    // the moment records and the end values (16 nx bytes or more each),
-    // which the prologue has not written yet
+    // E and J of the lifting use the sweep-constant array (16 nx bytes or
+    // more), K and dK the end values (16 nx bytes or more), dtJ the prefix
+    // sums (8 nx bytes): none written yet
     lift_block<G>(A, rin, A.rho_bar, lifted, reinterpret_cast<unsigned char*>(C.par),
-                  reinterpret_cast<unsigned char*>(C.part), reinterpret_cast<unsigned char*>(C.ends), red);
+                  reinterpret_cast<unsigned char*>(C.ends), reinterpret_cast<unsigned char*>(C.S), red);
     gin = lifted;
   }
 
@@ -504,18 +508,21 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     if constexpr (sizeof(G) == 4) ppe = __shfl_sync(0xffffffffu, pe, src);
     if constexpr (ADAPT) qq = __shfl_sync(0xffffffffu, q, src);
     if (valid && lig == 0) {
-      G* pr = C.part + 4 * (unsigned)i;
+      // pp (+ ppe): <v^+ g>; p (+ pe): sum over the negative velocities
       if constexpr (sizeof(G) == 4) {
-        *reinterpret_cast<float4*>(pr) = make_float4(pp, ppe, p, pe);
+        const ff t = two_sum(pp, p);  // compensated <v g>
+        const float e = __fadd_rn(__fadd_rn(ppe, pe), t.lo);
+        C.fk[i] = __fmaf_rn(t.hi, g_kflux, __fmul_rn(e, g_kflux));
+        C.mp[i] = __fadd_rn(pp, ppe);
+        C.mm[i] = -__fadd_rn(p, pe);
       } else {
-        pr[0] = pp; pr[1] = ppe; pr[2] = p; pr[3] = pe;
+        C.fk[i] = (pp + p) * g_kflux;
+        C.mp[i] = pp;
+        C.mm[i] = -p;
       }
       if constexpr (ADAPT) C.n2[i] = q + qq;
     }
   };
-  // m+ = <v^+ g>, m- = <v^- g> of an interface from its record
-  auto mplus = [&](int c) { return C.part[4 * c] + C.part[4 * c + 1]; };
-  auto mminus = [&](int c) { return -(C.part[4 * c + 2] + C.part[4 * c + 3]); };
 
   for (int base = 0; base < nx; base += ngrp) {  // warp-uniform trip count
     const int i = base + grp;
@@ -610,13 +617,14 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     C.base[tid] = M::add(rr[64 + w], ex_lane);   // prefix before this thread's chunk
     const R meanS = rr[96];
     __syncthreads();
-    G* eg = C.par;  // E^n goes through the par array's first slot first
-    for (int c = tid; c < nx; c += T) {
+    for (int c = tid; c < nx; c += T) {  // E^n into slots 0, 1 of the sweep constants
       const R E = M::sub(M::add(C.base[c >> lcpt], C.S[c]), meanS);
-      eg[4 * c + 3] = (G)M::tog(E);          // temporary: E in slot 3
-      if constexpr (ADAPT) {
-        if constexpr (sizeof(G) == 4) reinterpret_cast<ff*>(C.ed)[c] = E;
-        else { C.ed[c] = E; C.rd[c] = C.rho[c]; }
+      if constexpr (sizeof(G) == 4) {
+        *reinterpret_cast<ff*>(C.par + 4 * c) = E;
+      } else {
+        C.par[4 * c] = E;
+        C.par[4 * c + 1] = 0.0;
+        if constexpr (ADAPT) C.par[4 * c + 2] = C.rho[c];  // density copy for the criteria
       }
     }
     __syncthreads();  // rho final for this step; E of all cells visible
@@ -637,8 +645,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         // D2 f = (270 s1 - 27 s2 + 2 s3 - 490 f0) / 180,
         // D3 f = (-13 e1 + 8 e2 - e3) / 8, with e_k = f_{+k} - f_{-k},
         // s_k = f_{+k} + f_{-k} (then divided by dx^d).
-        ff* Ef = reinterpret_cast<ff*>(C.ed);
-        ff* Df = reinterpret_cast<ff*>(C.rd);
+        auto Ef = [&](int c) { return *reinterpret_cast<const ff*>(C.par + 4 * c); };
         ff* Jf = reinterpret_cast<ff*>(C.jd);
         const ff k1 = {A.f_k1, A.f_k1_lo};
         auto rho_f = [&](int c) { return C.rho[wrapi(c, nx)]; };
@@ -648,11 +655,11 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           const ff e2 = ff_sub_abs(rho_f(c + 2), rho_f(c - 2));
           const ff e3 = ff_sub_abs(rho_f(c + 3), rho_f(c - 3));
           const ff D1 = ff_mul(ff_add_abs(ff_sub_abs(ff_mul_f(e1, 45.f), ff_mul_f(e2, 9.f)), e3), k1);
-          ff Ec = ff_add_abs(Ef[wrapi(c - 1, nx)], Ef[c]);
+          ff Ec = ff_add_abs(Ef(wrapi(c - 1, nx)), Ef(c));
           Ec.hi *= 0.5f;
           Ec.lo *= 0.5f;
           const ff J = ff_sub_abs(D1, ff_mul(Ec, C.rho[c]));
-          Df[c] = D1;
+          C.par[4 * c + 2] = D1.hi;  // d rho / dx for the second pass
           Jf[c] = J;
           jsum = ff_add_abs(jsum, J);
         }
@@ -671,8 +678,8 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           const float d3J = n3.hi * A.f_k3;
           const float d2J = n2.hi * A.f_k2;
           const float d1J = (45.f * e1.hi - 9.f * e2.hi + e3.hi) * A.f_k1;
-          const float d1r = Df[c].hi, jc = J0.hi, rc = C.rho[c].hi;
-          const float Ec = 0.5f * (Ef[wrapi(c - 1, nx)].hi + Ef[c].hi);
+          const float d1r = C.par[4 * c + 2], jc = J0.hi, rc = C.rho[c].hi;
+          const float Ec = 0.5f * (C.par[4 * wrapi(c - 1, nx)] + C.par[4 * c]);
           const float Rc = -d3J + Ec * d2J + (2.f * rc - 3.f * rbf) * d1J + 2.f * jc * d1r - d1r * (jc - meanJ);
           const bool big_R = A.f_rfac * fabsf(Rc) > A.f_thr_R;
           const bool gl = C.n2[wrapi(c - 1, nx)] > A.f_thr_g2, gr = C.n2[c] > A.f_thr_g2;
@@ -688,8 +695,8 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         }
       } else {
         const double inv_dx = A.inv_dx;
-        auto rho_d = [&](int c) { return C.rd[wrapi(c, nx)]; };
-        auto E_d = [&](int c) { return C.ed[wrapi(c, nx)]; };
+        auto rho_d = [&](int c) { return C.par[4 * wrapi(c, nx) + 2]; };
+        auto E_d = [&](int c) { return C.par[4 * wrapi(c, nx)]; };
         double jsum = 0.0;
         for (int c = tid; c < nx; c += T) {
           double d1 = 0.0;
@@ -781,7 +788,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         const int c = k * T + tid;
         const bool wr = c < nx && (kin_cur[c] | kin_prev[c] | kin_prev2[c]);
         const unsigned b = __ballot_sync(0xffffffffu, wr);
-        if (wr) C.list[cnt[k * NW + w] + __popc(b & ((1u << l) - 1u))] = c;
+        if (wr) C.list[cnt[k * NW + w] + __popc(b & ((1u << l) - 1u))] = (uint16_t)c;
       }
     } else {
       count = nx;
@@ -792,14 +799,12 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     for (int c = tid; c < nx; c += T) {
       const int cl = wrapi(c - 1, nx), cr = wrapi(c + 1, nx);
       G* pr = C.par + 4 * c;
-      const G e = pr[3];
+      const G e = pr[0];
       const G J = M::flux_J(C.rho[c], C.rho[cr], e, g_inv_dx);
       const G ep = e > G(0) ? e : G(0), em = e < G(0) ? -e : G(0);
-      const G pm = ((mplus(c) - mplus(cl)) - (mminus(cr) - mminus(c))) * g_inv_dx;
+      const G pm = ((C.mp[c] - C.mp[cl]) - (C.mm[cr] - C.mm[c])) * g_inv_dx;
       const G* en = C.ends + 4 * c;
       const G gend = (G)0.5 * ((ep * en[2] - em * en[3]) - (ep * en[0] - em * en[1]));
-      pr[0] = ep * g_inv_dv;
-      pr[1] = em * g_inv_dv;
       pr[2] = pm + gend;
       pr[3] = J;
     }
@@ -813,16 +818,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   // density update from the fluxes of the new g: one flux per interface
   // (kinetic: dt/dx <xi g>/eps, fluid: dt/dx (-m2 J)), or the cell-based
   // rule of S^HMM when flux_rule == 1.
-  auto flux_kin = [&](int c) {
-    const G* pr = C.part + 4 * c;
-    if constexpr (sizeof(G) == 4) {  // compensated: (pos + neg) + (errors)
-      const ff t = two_sum(pr[0], pr[2]);
-      const float e = __fadd_rn(__fadd_rn(pr[1], pr[3]), t.lo);
-      return __fmaf_rn(t.hi, g_kflux, __fmul_rn(e, g_kflux));
-    } else {
-      return (pr[0] + pr[2]) * g_kflux;
-    }
-  };
+  auto flux_kin = [&](int c) { return C.fk[c]; };
   auto is_kin = [&](int c) { return ADAPT ? kin_cur[c] != 0 : true; };
   // J of an interface: slot 3 of its sweep constants
   auto Jat = [&](int c) { return C.par[4 * c + 3]; };
@@ -883,13 +879,16 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         if (kin) {
           const float4* pr4 = reinterpret_cast<const float4*>(C.par + 4 * i);
           G Ep, Em, Pp, Jv;
+          G Ev;
           if constexpr (sizeof(G) == 4) {
             const float4 q = *pr4;
-            Ep = q.x; Em = q.y; Pp = q.z; Jv = q.w;
+            Ev = q.x; Pp = q.z; Jv = q.w;
           } else {
             const G* pr = C.par + 4 * i;
-            Ep = pr[0]; Em = pr[1]; Pp = pr[2]; Jv = pr[3];
+            Ev = pr[0]; Pp = pr[2]; Jv = pr[3];
           }
+          Ep = Ev > G(0) ? Ev * g_inv_dv : G(0);
+          Em = Ev < G(0) ? -Ev * g_inv_dv : G(0);
           G Gl = first_lane ? G(0) : (Ep * left_nb - Em * Cc[0]);
 #pragma unroll
           for (int k = 0; k < VPT; ++k) {
