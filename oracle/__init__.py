@@ -61,7 +61,8 @@ class _PararealCfg(ctypes.Structure):
     _fields_ = [("t_end", ctypes.c_double), ("n_slices", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("coarse_kind", ctypes.c_int32), ("coarse_steps", ctypes.c_int32),
-                ("dt_fine", ctypes.c_double), ("lift_order", ctypes.c_int32)]
+                ("dt_fine", ctypes.c_double), ("lift_order", ctypes.c_int32),
+                ("mode", ctypes.c_int32)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -252,33 +253,35 @@ def lift(p: Params, rho, order: int = 1) -> np.ndarray:
     return g
 
 
-def _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order=1):
-    return _PararealCfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order)
+def _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order=1, mode=0):
+    return _PararealCfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order, mode)
 
 
 def parareal(p: Params, rho0, g0, t_end: float, n_slices: int, max_iter: int,
              tol: float = 0.0, coarse_kind: int = 0, coarse_steps: int = 1,
-             dt_fine: float | None = None, lift_order: int = 1):
-    """Algorithm 1; returns (rho_slices [(N+1), nx], errors, iterations)."""
+             dt_fine: float | None = None, lift_order: int = 1, mode: int = 0):
+    """Algorithm 1; returns (rho_slices [(N+1), nx], errors, iterations).
+    mode 0: density only with relifting; mode 1: full state (rho, g)."""
     rho0, g0 = _f64(rho0), _f64(g0)
     if dt_fine is None:
         dt_fine = dt_limit(p)
     out = np.empty((n_slices + 1, p.nx))
     err = np.zeros(max(max_iter, 1))
-    c = _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order)
+    c = _cfg(t_end, n_slices, max_iter, tol, coarse_kind, coarse_steps, dt_fine, lift_order, mode)
     it = _load().orc_parareal(ctypes.byref(p._c()), ctypes.byref(c), _dptr(rho0),
                               _dptr(g0), _dptr(out), _dptr(err))
     return out, err[:it], it
 
 
 def sequential(p: Params, rho0, g0, t_end: float, n_slices: int,
-               dt_fine: float | None = None, lift_order: int = 1) -> np.ndarray:
-    """Sequential fine reference with relifting at every slice boundary."""
+               dt_fine: float | None = None, lift_order: int = 1, mode: int = 0) -> np.ndarray:
+    """Sequential fine reference with relifting at every slice boundary
+    (mode 0), or the plain F carried through the slices (mode 1)."""
     rho0, g0 = _f64(rho0), _f64(g0)
     if dt_fine is None:
         dt_fine = dt_limit(p)
     out = np.empty((n_slices + 1, p.nx))
-    c = _cfg(t_end, n_slices, 0, 0.0, 0, 1, dt_fine, lift_order)
+    c = _cfg(t_end, n_slices, 0, 0.0, 0, 1, dt_fine, lift_order, mode)
     _load().orc_sequential(ctypes.byref(p._c()), ctypes.byref(c), _dptr(rho0),
                            _dptr(g0), _dptr(out))
     return out

@@ -559,9 +559,85 @@ static int64_t steps_for(double span, double dt_lim) {
 /* Algorithm 1 (Sec. 3.3) in the standard parareal reading of Sec. 3.1.
    The correction is evaluated as F + (G_new - G_old), which equals the
    printed G_new + F - G_old and is exact (bitwise F) on converged slices. */
+/* Algorithm 1 on the full micro-macro state U = (rho, g): F(U) is S^HMM
+   from the slice's own (rho, g) (no relifting), G(U) = (G rho, L G rho)
+   (the coarse density and its lifting), and the correction
+   U^{n+1,k+1} = F(U^{n,k}) + (G(U^{n,k+1}) - G(U^{n,k})) acts on both parts
+   (Sec. 3.1 applied to the state of the fine scheme).  Converged slices
+   equal the plain sequential F, without relifting.  The successive error is
+   measured on the density. */
+static int parareal_full(const orc_params* p, const orc_parareal_cfg* c,
+                         const double* rho0, const double* g0, double* rho_slices,
+                         double* err) {
+  const int nx = p->nx, nv = p->nv, N = c->n_slices;
+  const size_t G1 = (size_t)nx * nv;
+  const double span = c->t_end / N;
+  const int64_t nf = steps_for(span, c->dt_fine);
+  const double dtf = span / nf;
+  double* Gprev = malloc(sizeof(double) * (size_t)(N + 1) * nx);
+  double* Frho = malloc(sizeof(double) * (size_t)(N + 1) * nx);
+  double* Fg = malloc(sizeof(double) * (size_t)(N + 1) * G1);
+  double* next = malloc(sizeof(double) * (size_t)(N + 1) * nx);
+  double* gs = malloc(sizeof(double) * (size_t)(N + 1) * G1);     /* g^{n,k} */
+  double* gnext = malloc(sizeof(double) * (size_t)(N + 1) * G1);
+  double* tmp = malloc(sizeof(double) * nx);
+  double* lnew = malloc(sizeof(double) * G1);
+  double* lold = malloc(sizeof(double) * G1);
+
+  /* coarse guess U^{n+1,0} = G(U^{n,0}) */
+  memcpy(rho_slices, rho0, sizeof(double) * nx);
+  memcpy(gs, g0, sizeof(double) * G1);
+  for (int n = 0; n < N; ++n) {
+    memcpy(tmp, rho_slices + (size_t)n * nx, sizeof(double) * nx);
+    orc_coarse(p, c->coarse_kind, c->coarse_steps, span, tmp);
+    memcpy(rho_slices + (size_t)(n + 1) * nx, tmp, sizeof(double) * nx);
+    memcpy(Gprev + (size_t)(n + 1) * nx, tmp, sizeof(double) * nx);
+    relift(p, c, tmp, gs + (size_t)(n + 1) * G1);
+  }
+
+  int k = 0;
+  for (; k < c->max_iter && k < N; ++k) {
+    for (int n = k; n < N; ++n) {  /* F(U^{n,k}) */
+      double* r = Frho + (size_t)(n + 1) * nx;
+      double* g = Fg + (size_t)(n + 1) * G1;
+      memcpy(r, rho_slices + (size_t)n * nx, sizeof(double) * nx);
+      memcpy(g, gs + (size_t)n * G1, sizeof(double) * G1);
+      orc_fine(p, nf, dtf, r, g, NULL, NULL);
+    }
+    memcpy(next, rho_slices, sizeof(double) * (size_t)(k + 1) * nx);
+    memcpy(gnext, gs, sizeof(double) * (size_t)(k + 1) * G1);
+    for (int n = k; n < N; ++n) {
+      memcpy(tmp, next + (size_t)n * nx, sizeof(double) * nx);
+      orc_coarse(p, c->coarse_kind, c->coarse_steps, span, tmp);
+      double* out = next + (size_t)(n + 1) * nx;
+      const double* F = Frho + (size_t)(n + 1) * nx;
+      const double* Go = Gprev + (size_t)(n + 1) * nx;
+      for (int i = 0; i < nx; ++i) out[i] = F[i] + (tmp[i] - Go[i]);
+      relift(p, c, tmp, lnew);
+      relift(p, c, Go, lold);
+      double* gout = gnext + (size_t)(n + 1) * G1;
+      const double* FG = Fg + (size_t)(n + 1) * G1;
+      for (size_t q = 0; q < G1; ++q) gout[q] = FG[q] + (lnew[q] - lold[q]);
+      memcpy(Gprev + (size_t)(n + 1) * nx, tmp, sizeof(double) * nx);
+    }
+    double e = 0.0;
+    for (size_t q = 0; q < (size_t)(N + 1) * nx; ++q) {
+      const double d = fabs(next[q] - rho_slices[q]);
+      if (d > e) e = d;
+    }
+    memcpy(rho_slices, next, sizeof(double) * (size_t)(N + 1) * nx);
+    memcpy(gs, gnext, sizeof(double) * (size_t)(N + 1) * G1);
+    if (err) err[k] = e;
+    if (e < c->tol) { ++k; break; }
+  }
+  free(Gprev); free(Frho); free(Fg); free(next); free(gs); free(gnext); free(tmp); free(lnew); free(lold);
+  return k;
+}
+
 int orc_parareal(const orc_params* p, const orc_parareal_cfg* c,
                  const double* rho0, const double* g0, double* rho_slices,
                  double* err) {
+  if (c->mode == 1) return parareal_full(p, c, rho0, g0, rho_slices, err);
   const int nx = p->nx, nv = p->nv, N = c->n_slices;
   const double span = c->t_end / N;
   const int64_t nf = steps_for(span, c->dt_fine);
@@ -627,7 +703,7 @@ void orc_sequential(const orc_params* p, const orc_parareal_cfg* c,
     double* r = rho_slices + (size_t)(n + 1) * nx;
     memcpy(r, rho_slices + (size_t)n * nx, sizeof(double) * nx);
     if (n == 0) memcpy(g, g0, sizeof(double) * (size_t)nx * nv);
-    else relift(p, c, r, g);
+    else if (c->mode != 1) relift(p, c, r, g);  /* full state: g carried on */
     orc_fine(p, nf, dtf, r, g, NULL, NULL);
   }
   free(g);

@@ -141,6 +141,8 @@ typedef struct {
   int32_t coarse_kind, coarse_steps;
   double dt_fine;     /* fine step limit; per slice n = ceil(slice/dt_fine) */
   int32_t lift_order; /* L of the relifting (0 or 1: order one) */
+  int32_t mode;       /* 0: density only, relifted at every slice (Alg. 1);
+                         1: full state (rho, g), G(U) = (G rho, L G rho) */
 } orc_parareal_cfg;
 
 /* Algorithm 1 (Sec. 3.3): rho-only parareal with relifting.
@@ -152,7 +154,8 @@ int orc_parareal(const orc_params* p, const orc_parareal_cfg* c,
 
 /* sequential fine reference of the same problem: rho^{n+1} =
    F_rho(rho^n, L rho^n) (g0 for the first slice), with the lifting of
-   order c->lift_order */
+   order c->lift_order; with c->mode == 1, the plain F carried through the
+   slices without relifting */
 void orc_sequential(const orc_params* p, const orc_parareal_cfg* c,
                     const double* rho0, const double* g0, double* rho_slices);
 

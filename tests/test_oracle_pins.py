@@ -482,6 +482,34 @@ def test_parareal_first_k_slices_equal_sequential(k, L):
         assert np.abs(out[k + 1:] - seq[k + 1:]).max() > 0.0
 
 
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_full_state_parareal_first_k_slices_equal_plain_F(k):
+    """Full-state mode (U = (rho, g), G(U) = (G rho, L G rho)): after k
+    iterations the first k+1 slices are the plain sequential F carried
+    through the slices without relifting (the parareal property of
+    Sec. 3.1 for the state of the fine scheme), bitwise; at K = N, all of
+    them.  The plain reference is F composed slice by slice, written out
+    here, not the oracle's sequential routine."""
+    w, p = _parareal_case()
+    dt = O.dt_limit(p)
+    span = w.t_end / w.n_slices
+    nf = int(math.ceil(span / dt))
+    plain = [w.rho0.copy()]
+    r, g = w.rho0.copy(), w.g0.copy()
+    for n in range(w.n_slices):
+        r, g, _, _ = O.fine(p, nf, span / nf, r, g)
+        plain.append(r.copy())
+    plain = np.array(plain)
+    out, err, it = O.parareal(p, w.rho0, w.g0, w.t_end, w.n_slices, k, mode=1)
+    assert it == k
+    assert np.array_equal(out[: k + 1], plain[: k + 1])
+    full, _, _ = O.parareal(p, w.rho0, w.g0, w.t_end, w.n_slices, w.n_slices, mode=1)
+    assert np.array_equal(full, plain)
+    # the density-only mode converges to the relifted sequence instead
+    rho_only, _, _ = O.parareal(p, w.rho0, w.g0, w.t_end, w.n_slices, w.n_slices)
+    assert np.abs(rho_only[2:] - plain[2:]).max() > 0.0
+
+
 def test_parareal_converges_everywhere_at_K_equals_N():
     w, p = _parareal_case()
     seq = O.sequential(p, w.rho0, w.g0, w.t_end, w.n_slices)
