@@ -293,11 +293,23 @@ MM_API mm_status mm_coarse(mm_ctx* ctx, int32_t batch, double t_span,
 MM_API mm_status mm_lift(mm_ctx* ctx, int32_t batch, const double* rho, void* g_out,
                   void* stream);
 
+typedef enum {
+  MM_PARAREAL_RHO_LIFT = 0,   /* Algorithm 1: the density is the parareal
+                                 unknown; every fine propagation starts from
+                                 the lifted density (Sec. 3.2-3.3) */
+  MM_PARAREAL_FULL_STATE = 1  /* the fine scheme's state U = (rho, g) is the
+                                 unknown: F(U) from the slice's own (rho, g),
+                                 G(U) = (G rho, L G rho), the correction on
+                                 both parts; converges to the plain
+                                 sequential F (parareal_run only) */
+} mm_parareal_mode;
+
 typedef struct {
   double t_end;        /* T */
   int32_t n_slices;    /* N_g >= 1 */
   int32_t max_iter;    /* K >= 0 (capped at N_g) */
   double tol;          /* stop when the successive error is below tol */
+  int32_t mode;        /* mm_parareal_mode (0 = MM_PARAREAL_RHO_LIFT) */
 } mm_parareal_cfg;
 
 typedef struct {
@@ -312,13 +324,17 @@ typedef struct {
 } mm_parareal_stats;
 
 /* Algorithm 1 (Sec. 3.3) with F = S^HMM, G = S^0 and the lifting of order
-   one: coarse guess, then per iteration k the fine propagations of all
-   slices n >= k in one batched launch, the sequential correction
-   rho^{n+1,k+1} = F(rho^{n,k}) + (G(rho^{n,k+1}) - G(rho^{n,k})) on the
-   device, relifting, and the successive error max |rho^{n,k+1}-rho^{n,k}|.
-   The first slice starts from (rho0, g0); later slices from their lifted
-   density.  rho_slices_out [n_slices + 1][nx] double receives rho^{n,K}.
-   The call synchronises the stream once per iteration (error test).
+   params.lift_order: coarse guess, then per iteration k the fine
+   propagations of all slices n >= k in one batched launch, the sequential
+   correction rho^{n+1,k+1} = F(rho^{n,k}) + (G(rho^{n,k+1}) - G(rho^{n,k}))
+   on the device, relifting, and the successive error
+   max |rho^{n,k+1} - rho^{n,k}|.  The first slice starts from (rho0, g0);
+   later slices from their lifted density.  With cfg.mode ==
+   MM_PARAREAL_FULL_STATE the slices carry (rho, g): F starts from the
+   slice's own g, and g^{n+1,k+1} = F_g(U^{n,k}) + (L G rho^{n,k+1} -
+   L G rho^{n,k}) (the slices' g stay on the device, 2 (N+1) nx nv values).
+   rho_slices_out [n_slices + 1][nx] double receives rho^{n,K}.  The call
+   synchronises the stream once per iteration (error test).
    Errors: MM_ERR_INVALID, MM_ERR_UNSTABLE, MM_ERR_CUDA, MM_ERR_OOM. */
 MM_API mm_status parareal_run(mm_ctx* ctx, const mm_parareal_cfg* cfg,
                        const double* rho0, const void* g0,
@@ -348,8 +364,10 @@ typedef struct mm_batch mm_batch;
 MM_API size_t mm_batch_footprint(const mm_params* p, const mm_parareal_cfg* cfg);
 MM_API mm_status mm_batch_create(const mm_alloc* alloc, mm_batch** out);
 /* Copy a solve's initial data (host or device arrays rho0 [nx], g0 [nx][nv]
-   in the params' precision) into the batch.  Errors: MM_ERR_INVALID
-   (parameters, configuration, unsupported nv), MM_ERR_OOM, MM_ERR_CUDA. */
+   in the params' precision) into the batch.  The batch runs the density
+   mode of Algorithm 1 (cfg.mode must be MM_PARAREAL_RHO_LIFT).
+   Errors: MM_ERR_INVALID (parameters, configuration, unsupported nv),
+   MM_ERR_OOM, MM_ERR_CUDA. */
 MM_API mm_status mm_batch_add(mm_batch* b, const mm_params* p, const mm_parareal_cfg* cfg,
                        const double* rho0, const void* g0, uint64_t* id);
 /* One parareal iteration of every unfinished solve; *active (nullable)
@@ -403,17 +421,24 @@ typedef struct {
   int64_t kinetic_updates;
 } mm_result;
 
-/* Serving loop with continuous batching.  One scheduler thread owns an
-   mm_batch and a stream and runs rounds: it admits queued requests (first
-   come, first served) while their device footprint fits hbm_budget_bytes
-   and fewer than max_slots solves are resident, runs one parareal
-   iteration of every resident solve (all their fine propagations in one
-   persistent work-list launch), and completes the solves that finished.
-   A request's footprint is mm_batch_footprint plus its share of the fine
-   kernel's step buffers (two states per SM) plus 1 MiB.  Requests that
-   arrive while others run join at the next round; a result does not depend
-   on the requests it ran with.  If a round fails, the solves resident in
-   it fail with its status and the server continues with the queue.
+/* Serving loop with continuous batching.  Two lanes, each one scheduler
+   thread that owns an mm_batch and a stream, run rounds: a lane admits its
+   queued requests (first come, first served) while their device footprint
+   fits hbm_budget_bytes (shared by both lanes) and fewer than max_slots
+   solves are resident, runs one parareal iteration of every resident solve
+   of the lane (all their fine propagations in one persistent work-list
+   launch), and completes the solves that finished.  A request whose
+   parareal iteration costs more than 2e10 fine cell-updates (estimated from
+   the step rule: nx nv n_slices steps-per-slice) goes to the long lane, the
+   others to the short lane; the long lane's launches leave one eighth of
+   the SMs to the short lane, so small requests do not wait behind rounds of
+   large ones (the short lane uses every SM while no long solve is
+   resident).  A request's footprint is mm_batch_footprint plus its share of
+   the fine kernel's step buffers (two states per SM) plus 1 MiB.  Requests
+   that arrive while others run join their lane at its next round; a result
+   does not depend on the requests it ran with.  If a round fails, the
+   solves resident in that lane fail with its status and the lane continues
+   with its queue.
    Errors: MM_ERR_INVALID, MM_ERR_CUDA, MM_ERR_OOM. */
 MM_API mm_status mm_server_create(const mm_server_cfg* cfg, const mm_alloc* alloc,
                            mm_server** out);

@@ -84,7 +84,7 @@ struct Workspace {
 
 enum WsSlot {
   WS_GBUF1 = 0, WS_COLS, WS_RHO_IN, WS_RHO_OUT, WS_G_IN, WS_G_OUT, WS_MASK, WS_MACRO,
-  WS_STATUS, WS_PR_RHO, WS_PR_F, WS_PR_G, WS_PR_GB, WS_PR_ERR, WS_COUNT
+  WS_STATUS, WS_PR_RHO, WS_PR_F, WS_PR_G, WS_PR_GB, WS_PR_ERR, WS_PR_GB2, WS_PR_GOLD, WS_PR_LD, WS_COUNT
 };
 
 }  // namespace
@@ -319,13 +319,19 @@ extern "C" mm_status mm_create(const mm_params* p, const mm_alloc* alloc, mm_ctx
     tab[5 * nv + j] = v;
   }
   std::vector<float> tabf(tab.begin(), tab.end());
-  cudaError_t e = cudaMalloc(&c->d_vtab, tab.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_vtab_f, tabf.size() * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_vtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_vtab_f, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  // stream-ordered allocation on the legacy stream: no device-wide
+  // synchronisation, so contexts can come and go while other streams run
+  cudaError_t e = cudaMallocAsync(&c->d_vtab, tab.size() * sizeof(double), 0);
+  if (e == cudaSuccess) e = cudaMallocAsync(&c->d_vtab_f, tabf.size() * sizeof(float), 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_vtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_vtab_f, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
-    cudaFree(c->d_vtab);
-    cudaFree(c->d_vtab_f);
+    if (c->d_vtab) cudaFreeAsync(c->d_vtab, 0);
+    if (c->d_vtab_f) cudaFreeAsync(c->d_vtab_f, 0);
+    cudaStreamSynchronize(0);
     delete c;
     return mm_cuda_fail(e, "mm_create: velocity table");
   }
@@ -336,10 +342,20 @@ extern "C" mm_status mm_create(const mm_params* p, const mm_alloc* alloc, mm_ctx
 extern "C" void mm_destroy(mm_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  c->ws.release_all(0);
+  mmk::ctx_release(c, 0);
   cudaStreamSynchronize(0);
-  cudaFree(c->d_vtab);
-  cudaFree(c->d_vtab_f);
+}
+
+// Free a context's device memory in stream order on s, without a
+// device-wide synchronisation (the batch engine: its solves' contexts have
+// no work in flight once the batch's stream is synchronised, while another
+// batch may be running on another stream).
+void mmk::ctx_release(mm_ctx* c, cudaStream_t s) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  c->ws.release_all(s);
+  if (c->d_vtab) cudaFreeAsync(c->d_vtab, s);
+  if (c->d_vtab_f) cudaFreeAsync(c->d_vtab_f, s);
   delete c;
 }
 
@@ -749,6 +765,9 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   if (!c || !cfg) return mm_fail(MM_ERR_INVALID, "NULL argument");
   if (cfg->n_slices < 1 || cfg->max_iter < 0 || !(cfg->t_end > 0))
     return mm_fail(MM_ERR_INVALID, "bad parareal configuration");
+  if (cfg->mode != MM_PARAREAL_RHO_LIFT && cfg->mode != MM_PARAREAL_FULL_STATE)
+    return mm_fail(MM_ERR_INVALID, "cfg.mode must be MM_PARAREAL_RHO_LIFT or MM_PARAREAL_FULL_STATE");
+  const bool full = cfg->mode == MM_PARAREAL_FULL_STATE;
   if (!rho0 || !g0 || !rho_slices_out) return mm_fail(MM_ERR_INVALID, "NULL array");
   if (c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
     return mm_fail(MM_ERR_UNSTABLE, "params.dt is above the stability limit");
@@ -775,8 +794,17 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     return st;
   if ((st = c->ws.get(WS_PR_F, rowb * (N + 1), s, &frho)) != MM_OK) return st;
   if ((st = c->ws.get(WS_PR_G, rowb * (N + 1), s, &gprev)) != MM_OK) return st;
-  if ((st = c->ws.get(WS_PR_GB, (size_t)N * nx * nv * gsz, s, &gb)) != MM_OK) return st;
+  const size_t G1 = (size_t)nx * nv * gsz;  // bytes of one slice's g
+  if ((st = c->ws.get(WS_PR_GB, (size_t)(full ? N + 1 : N) * G1, s, &gb)) != MM_OK) return st;
   if ((st = c->ws.get(WS_PR_ERR, 64, s, &errp)) != MM_OK) return st;
+  // full state: the slices' g of the next iterate, the coarse densities
+  // before the correction, and the scratch of the lifted differences
+  void *gb2 = nullptr, *gold = nullptr, *ldws = nullptr;
+  if (full) {
+    if ((st = c->ws.get(WS_PR_GB2, (size_t)(N + 1) * G1, s, &gb2)) != MM_OK) return st;
+    if ((st = c->ws.get(WS_PR_GOLD, rowb * (N + 1), s, &gold)) != MM_OK) return st;
+    if ((st = c->ws.get(WS_PR_LD, mmk::lift_diff_ws_bytes(nx, N), s, &ldws)) != MM_OK) return st;
+  }
 
   // initial slice and rho_bar (mean of the initial density when NaN)
   CK(cudaMemcpyAsync(rho, rho0, rowb, cudaMemcpyDefault, s), "copy rho0");
@@ -802,29 +830,35 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   const int K = std::min(cfg->max_iter, N);
   for (int k = 0; k < K; ++k) {
     const int batch = N - k;
-    // inputs of the fine propagations: (rho^{n,k}, g^{n,k}), n = k..N-1
+    // inputs of the fine propagations: (rho^{n,k}, g^{n,k}), n = k..N-1.
+    // Density mode: g relifted from the density into gb[0..batch) (slice 0
+    // from g0).  Full state: the slices' own g, kept at gb[n] (lifted once
+    // from the coarse guess).
     if (k == 0) {
       CK(cudaMemcpyAsync(gb, g0, (size_t)nx * nv * gsz, cudaMemcpyDefault, s), "copy g0");
       if (N > 1) {
         mmk::MacroArgs la = macro_args(c, N - 1, span, rb);
-        e = mmk::launch_lift(la, (const double*)rho + nx, (char*)gb + (size_t)nx * nv * gsz, fp32,
-                             (double*)gws, s);
+        e = mmk::launch_lift(la, (const double*)rho + nx, (char*)gb + G1, fp32, (double*)gws, s);
       }
-    } else {
+    } else if (!full) {
       mmk::MacroArgs la = macro_args(c, batch, span, rb);
       e = mmk::launch_lift(la, (const double*)rho + (size_t)k * nx, gb, fp32, (double*)gws, s);
     }
     if (e != cudaSuccess) return mm_cuda_fail(e, "lift");
+    void* g_in = full ? (void*)((char*)gb + (size_t)k * G1) : gb;
+    void* g_out = full ? (void*)((char*)gb2 + (size_t)(k + 1) * G1) : gb;  // full: F_g(U^{n,k}) at n+1
     mm_fine_stats fs;
-    st = fine_impl(c, batch, nf, dtf, (const double*)rho + (size_t)k * nx, gb, (double*)frho + (size_t)(k + 1) * nx,
-                   gb, nullptr, rb, stats ? &fs : nullptr, s);
+    st = fine_impl(c, batch, nf, dtf, (const double*)rho + (size_t)k * nx, g_in,
+                   (double*)frho + (size_t)(k + 1) * nx, g_out, nullptr, rb, stats ? &fs : nullptr, s);
     if (st != MM_OK) return st;
     if (stats) {
       kin_total += fs.kinetic_updates;
       fine_ms += fs.elapsed_ms;
       ++fine_launches;
     }
-    // sequential correction on the device
+    // sequential correction on the device (the coarse values before it are
+    // kept for the full-state g correction)
+    if (full) CK(cudaMemcpyAsync(gold, gprev, rowb * (N + 1), cudaMemcpyDeviceToDevice, s), "save G");
     mmk::CorrectArgs ca{};
     ca.m = ma;
     ca.n_slices = N;
@@ -835,6 +869,14 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     ca.err = (double*)errp;
     e = mmk::launch_correct(ca, (double*)gws, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
+    if (full) {  // g^{n+1,k+1} = F_g(U^{n,k}) + (L G rho^{n,k+1} - L G rho^{n,k}), n = k..N-1
+      mmk::MacroArgs la = macro_args(c, batch, span, rb);
+      e = mmk::launch_lift_diff(la, (const double*)gprev + (size_t)(k + 1) * nx,
+                                (const double*)gold + (size_t)(k + 1) * nx, (char*)gb2 + (size_t)(k + 1) * G1,
+                                fp32, (double*)ldws, s);
+      if (e != cudaSuccess) return mm_cuda_fail(e, "full-state correction");
+      std::swap(gb, gb2);
+    }
     double err = 0;
     CK(cudaMemcpyAsync(&err, errp, 8, cudaMemcpyDeviceToHost, s), "read error");
     CK(cudaStreamSynchronize(s), "parareal: synchronise");
@@ -935,6 +977,15 @@ mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out)
 // ------------------------------------------- context access for batches --
 
 const mm_params& mmk::ctx_params(const mm_ctx* c) { return c->p; }
+double mmk::solve_iteration_cost(const mm_params& p, const mm_parareal_cfg& cfg) {
+  if (p.nv < 4 || p.nx < 1 || cfg.n_slices < 1 || !(cfg.t_end > 0)) return 0.0;
+  mm_params q = p;
+  if (q.cfl_theta == 0) q.cfl_theta = 0.9;
+  const mmk::VelocityGrid vg = build_velocity_grid(p.nv, p.v_max);
+  const double lim = q.dt > 0 ? q.dt : q.cfl_theta * stability_limit(q, vg.m2);
+  const double steps = (double)steps_for(cfg.t_end / cfg.n_slices, lim);
+  return (double)p.nx * p.nv * cfg.n_slices * steps;
+}
 int mmk::ctx_device(const mm_ctx* c) { return c->device; }
 int64_t mmk::ctx_fine_steps(const mm_ctx* c, double span) { return steps_for(span, c->dt_limit); }
 mmk::MacroArgs mmk::ctx_macro_args(const mm_ctx* c, double span, double rho_bar) {

@@ -47,6 +47,7 @@ struct mm_batch {
   bool has_cb = false;
   int device = 0;
   int n_sm = 0;
+  int max_ctas = 0;  // cap on the work-list launch's CTAs (0: one per SM)
   uint64_t next_id = 1;
   std::map<uint64_t, std::unique_ptr<Solve>> solves;
   size_t bytes_in_use = 0;
@@ -89,7 +90,7 @@ struct mm_batch {
     dfree(v.g0, s);
     v.rho = v.frho = v.gprev = nullptr;
     v.g0 = nullptr;
-    if (v.ctx) mm_destroy(v.ctx);
+    if (v.ctx) mmk::ctx_release(v.ctx, s);
     v.ctx = nullptr;
     bytes_in_use -= v.bytes;
   }
@@ -121,12 +122,14 @@ extern "C" mm_status mm_batch_add(mm_batch* b, const mm_params* p, const mm_para
   if (!b || !p || !cfg || !rho0 || !g0 || !id) return mm_fail(MM_ERR_INVALID, "NULL argument");
   if (cfg->n_slices < 1 || cfg->max_iter < 0 || !(cfg->t_end > 0))
     return mm_fail(MM_ERR_INVALID, "bad parareal configuration");
+  if (cfg->mode != MM_PARAREAL_RHO_LIFT)
+    return mm_fail(MM_ERR_INVALID, "batch: only the density mode of Algorithm 1 (MM_PARAREAL_RHO_LIFT)");
   cudaSetDevice(b->device);
   std::unique_ptr<Solve> v(new Solve());
   mm_status st = mm_create(p, b->has_cb ? &b->cb : nullptr, &v->ctx);
   if (st != MM_OK) return st;
   if (!mmk::ctx_list_layout(v->ctx, &v->lanes)) {
-    mm_destroy(v->ctx);
+    mmk::ctx_release(v->ctx, 0);
     return mm_fail(MM_ERR_INVALID, "batch: nv needs 8 velocity nodes per lane (FP32) or 4 (FP64)");
   }
   v->cfg = *cfg;
@@ -264,7 +267,8 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
     for (size_t q = 0; q < order.size(); ++q) sorted[q] = items[order[q]];
     ws_g = (ws_g + 255) & ~size_t(255);
     ws_col = (ws_col + 255) & ~size_t(255);
-    const int grid = (int)std::min<size_t>(sorted.size(), (size_t)b->n_sm);
+    const int cap = b->max_ctas > 0 ? std::min(b->max_ctas, b->n_sm) : b->n_sm;
+    const int grid = (int)std::min<size_t>(sorted.size(), (size_t)cap);
     const size_t per_cta = 2 * ws_g + ws_col;
     if ((st = b->grow(b->fine_ws, per_cta * grid, s)) != MM_OK) return st;
     const size_t tb = sizeof(mmk::FineListSolve) * tab.size();
@@ -423,4 +427,8 @@ extern "C" mm_status parareal_run_many(int32_t n, const mm_params* params, const
     st = mm_batch_take(b, ids[q], rho_slices_out[q], stats ? stats + q : nullptr);
   mm_batch_destroy(b);
   return st;
+}
+
+void mmk::batch_set_max_ctas(mm_batch* b, int n) {
+  if (b) b->max_ctas = n > 0 ? n : 0;
 }

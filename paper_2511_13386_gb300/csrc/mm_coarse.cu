@@ -258,6 +258,65 @@ __global__ void lift_kernel(MacroArgs a, const double* rho, G* g, double* gws, i
   }
 }
 
+// Lifted difference of the full-state correction, one CTA per slice:
+// g[b] += L rho_new[b] - L rho_old[b] (lifting of order a.lift_order).  Both
+// liftings are formed in double and subtracted before the addition, so a
+// slice whose coarse value did not change keeps its fine g bitwise.  ws: 12
+// arrays of nx doubles per CTA in global memory.
+template <class G>
+__global__ void lift_diff_kernel(MacroArgs a, const double* rho_new, const double* rho_old, G* g, double* ws) {
+  __shared__ double red[64];
+  const int nx = a.nx, nv = a.nv, T = blockDim.x;
+  double* base = ws + (size_t)blockIdx.x * 12 * nx;
+  double* R[2] = {base, base + 6 * nx};  // rho, E, J, K, dK, dtJ per density
+  const double* src[2] = {rho_new + (size_t)blockIdx.x * nx, rho_old + (size_t)blockIdx.x * nx};
+  for (int d = 0; d < 2; ++d) {
+    double* rho = R[d];
+    double* E = rho + nx;
+    double* J = rho + 2 * nx;
+    for (int i = threadIdx.x; i < nx; i += T) rho[i] = src[d][i];
+    __syncthreads();
+    poisson_block(rho, E, nx, a.rho_bar, a.dx, red);
+    for (int i = threadIdx.x; i < nx; i += T) {
+      const double r0 = rho[i], r1 = rho[i + 1 == nx ? 0 : i + 1];
+      J[i] = (r1 - r0) * a.inv_dx - E[i] * 0.5 * (r0 + r1);
+    }
+    __syncthreads();
+    if (a.lift_order >= 2) lift_fields(rho, E, J, rho + 3 * nx, rho + 4 * nx, rho + 5 * nx, nx, a.inv_dx, red);
+  }
+  const double* vM = a.vtab + 2 * nv;
+  const double* Mj = a.vtab + 1 * nv;
+  const double* vj = a.vtab + 5 * nv;
+  const LiftConsts lc{a.lift_order, a.eps, a.xiM, a.m2, a.mu3};
+  G* gb = g + (size_t)blockIdx.x * nx * nv;
+  const size_t n = (size_t)nx * nv;
+  for (size_t q = threadIdx.x; q < n; q += T) {
+    const int i = (int)(q / nv), j = (int)(q % nv);
+    double l[2];
+    for (int d = 0; d < 2; ++d) {
+      const double* rho = R[d];
+      if (a.lift_order <= 1) {
+        const double J = rho[2 * nx + i];
+        l[d] = -a.eps * (vM[j] * J - a.xiM * J * Mj[j]);
+      } else {
+        l[d] = lift_value(lc, vj[j], Mj[j], rho[nx + i], rho[2 * nx + i], rho[3 * nx + i], rho[4 * nx + i],
+                          rho[5 * nx + i]);
+      }
+    }
+    gb[q] = (G)((double)gb[q] + (l[0] - l[1]));
+  }
+}
+
+size_t lift_diff_ws_bytes(int nx, int batch) { return (size_t)batch * 12 * nx * sizeof(double); }
+
+cudaError_t launch_lift_diff(const MacroArgs& a, const double* rho_new, const double* rho_old, void* g, bool fp32,
+                             double* ws, cudaStream_t s) {
+  if (a.batch <= 0) return cudaSuccess;
+  if (fp32) lift_diff_kernel<float><<<a.batch, kMacroThreads, 0, s>>>(a, rho_new, rho_old, (float*)g, ws);
+  else lift_diff_kernel<double><<<a.batch, kMacroThreads, 0, s>>>(a, rho_new, rho_old, (double*)g, ws);
+  return cudaGetLastError();
+}
+
 // Sequential correction of Algorithm 1 for one solve (one CTA):
 // for n = k..N-1: Gn = G(rho^{n,k+1}); rho^{n+1,k+1} = F + (Gn - Gprev);
 // Gprev = Gn; err = max |rho^{n+1,k+1} - rho^{n+1,k}|.

@@ -144,6 +144,11 @@ cudaError_t launch_coarse(const MacroArgs& a, const double* rho_in, double* rho_
                           cudaStream_t s);
 cudaError_t launch_lift(const MacroArgs& a, const double* rho, void* g_out, bool fp32, double* gws,
                         cudaStream_t s);
+// Full-state parareal: g[b] += L rho_new[b] - L rho_old[b] for a.batch
+// densities; ws holds lift_diff_ws_bytes(nx, batch) bytes.
+size_t lift_diff_ws_bytes(int nx, int batch);
+cudaError_t launch_lift_diff(const MacroArgs& a, const double* rho_new, const double* rho_old, void* g, bool fp32,
+                             double* ws, cudaStream_t s);
 
 // Parareal on the device: the sequential correction sweep over slices
 // n = k..N-1 (one CTA per solve), and the successive-error reduction.
@@ -175,6 +180,9 @@ struct FinePlan {
 };
 mm_status fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out);
 
+// Free a context without a device-wide synchronisation (stream-ordered on s).
+void ctx_release(mm_ctx* c, cudaStream_t s);
+
 // Context access for the batch engine (mm_batch.cpp).
 const mm_params& ctx_params(const mm_ctx* c);
 int ctx_device(const mm_ctx* c);
@@ -182,6 +190,13 @@ int64_t ctx_fine_steps(const mm_ctx* c, double span);
 MacroArgs ctx_macro_args(const mm_ctx* c, double span, double rho_bar);
 FineArgs ctx_fine_args(const mm_ctx* c, int64_t n, double dt, double rho_bar);  // pointers unset
 bool ctx_list_layout(const mm_ctx* c, int* lanes);
+// Fine cell-updates of one parareal iteration of a solve (every slice, the
+// whole window of steps, all cells), from the step rule on the host: the
+// serving scheduler's cost estimate.
+double solve_iteration_cost(const mm_params& p, const mm_parareal_cfg& c);
+// Cap on the CTAs of a batch's work-list launch (0: one per SM); lets two
+// batches share the GPU on disjoint SMs.
+void batch_set_max_ctas(mm_batch* b, int n);
 double ctx_mean(const double* rho, int nx);
 
 }  // namespace mmk

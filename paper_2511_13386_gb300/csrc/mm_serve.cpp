@@ -2,16 +2,26 @@
 // batching.
 //
 // Requests carry a full problem (parameters, parareal configuration, host
-// initial data).  One scheduler thread owns a batch (mm_batch.cpp) and a
-// stream, and runs rounds: it admits queued requests while their device
-// footprint fits the HBM budget and a slot is free, runs one parareal
-// iteration of every resident solve (the fine propagations of all of them
-// share one persistent work-list launch), and hands out the solves that
-// finished.  A request that arrives while others are on the GPU joins at the
-// next round; its result does not depend on which other solves it ran with.
+// initial data).  Two lanes, each a scheduler thread that owns a batch
+// (mm_batch.cpp) and a stream, run rounds: admit queued requests of the lane
+// while their device footprint fits the HBM budget (shared by the lanes) and
+// a slot is free, run one parareal iteration of every resident solve of the
+// lane (the fine propagations of all of them share one persistent work-list
+// launch), and hand out the solves that finished.  A request that arrives
+// while others are on the GPU joins its lane at the next round; its result
+// does not depend on which other solves it ran with.
+//
+// Lanes: a request whose parareal iteration costs more than kLongCost fine
+// cell-updates (estimated from the step rule) goes to the long lane, every
+// other one to the short lane.  The long lane's launches use at most
+// n_sm - n_sm/8 CTAs, so one eighth of the SMs stays free for the short
+// lane: a small request does not wait behind a round of large solves that
+// takes seconds.  While the long lane has nothing resident, the short lane's
+// launches may use every SM.
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -27,6 +37,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// fine cell-updates per parareal iteration above which a request is long
+constexpr double kLongCost = 2e10;
+
 struct Job {
   uint64_t ticket = 0;
   mm_params params{};
@@ -34,6 +47,7 @@ struct Job {
   std::vector<double> rho0;
   std::vector<unsigned char> g0;
   size_t footprint = 0;
+  int lane = 0;
   Clock::time_point t_submit;
   uint64_t batch_id = 0;
   // result
@@ -55,13 +69,14 @@ struct mm_server {
   int n_sm = 1;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
-  std::deque<std::shared_ptr<Job>> queue;
+  std::deque<std::shared_ptr<Job>> queue[2];       // per lane: 0 short, 1 long
   std::map<uint64_t, std::shared_ptr<Job>> jobs;  // by ticket, until polled
   size_t in_use = 0;
   int running = 0;
+  std::atomic<int> long_resident{0};
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::thread sched;
+  std::thread sched[2];
 
   // device bytes a request holds while resident: its arrays plus its share
   // of the fine kernel's per-CTA step buffers (sized for the largest state)
@@ -77,28 +92,35 @@ struct mm_server {
     j->done = true;
     in_use -= j->footprint;
     --running;
+    if (j->lane == 1) --long_resident;
     cv_done.notify_all();
+    cv_sched.notify_all();  // freed budget may admit a request of the other lane
   }
 
-  void scheduler() {
+  void scheduler(int lane) {
     cudaSetDevice(device);
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     mm_batch* batch = nullptr;
     mm_status bst = mm_batch_create(has_alloc ? &alloc : nullptr, &batch);
+    const int reserve = n_sm >= 16 ? n_sm / 8 : 0;  // SMs kept for the short lane
     std::map<uint64_t, std::shared_ptr<Job>> inflight;  // by batch id
     while (true) {
       std::vector<std::shared_ptr<Job>> admit;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_sched.wait(lk, [&] { return stop || !queue.empty() || !inflight.empty(); });
+        auto& q = queue[lane];
+        cv_sched.wait(lk, [&] {
+          return stop || !inflight.empty() ||
+                 (!q.empty() && running < cfg.max_slots && in_use + q.front()->footprint <= cfg.hbm_budget_bytes);
+        });
         if (stop) break;
-        while (!queue.empty() && running < cfg.max_slots &&
-               in_use + queue.front()->footprint <= cfg.hbm_budget_bytes) {
-          admit.push_back(queue.front());
-          in_use += queue.front()->footprint;
+        while (!q.empty() && running < cfg.max_slots && in_use + q.front()->footprint <= cfg.hbm_budget_bytes) {
+          admit.push_back(q.front());
+          in_use += q.front()->footprint;
           ++running;
-          queue.pop_front();
+          if (lane == 1) ++long_resident;
+          q.pop_front();
         }
       }
       for (auto& j : admit) {
@@ -111,6 +133,8 @@ struct mm_server {
         else inflight[j->batch_id] = j;
       }
       if (inflight.empty()) continue;
+      if (bst == MM_OK)
+        mmk::batch_set_max_ctas(batch, lane == 1 ? n_sm - reserve : (long_resident.load() > 0 ? reserve : n_sm));
       int32_t active = 0;
       mm_status st = mm_batch_step(batch, &active, s);
       if (st != MM_OK) {  // the round failed: every resident solve fails with it
@@ -160,7 +184,7 @@ extern "C" mm_status mm_server_create(const mm_server_cfg* cfg, const mm_alloc* 
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
   if (s->n_sm <= 0) s->n_sm = 1;
-  s->sched = std::thread([s] { s->scheduler(); });
+  for (int lane = 0; lane < 2; ++lane) s->sched[lane] = std::thread([s, lane] { s->scheduler(lane); });
   *out = s;
   return MM_OK;
 }
@@ -178,6 +202,7 @@ extern "C" mm_status serve_submit(mm_server* s, const mm_request* req, uint64_t*
   j->g0.resize(gb);
   memcpy(j->g0.data(), req->g0, gb);
   j->footprint = s->footprint_of(p, req->cfg);
+  j->lane = mmk::solve_iteration_cost(p, req->cfg) > kLongCost ? 1 : 0;
   if (j->footprint > s->cfg.hbm_budget_bytes)
     return mm_fail(MM_ERR_INVALID, "request footprint exceeds the whole HBM budget");
   j->t_submit = Clock::now();
@@ -185,7 +210,7 @@ extern "C" mm_status serve_submit(mm_server* s, const mm_request* req, uint64_t*
   if (s->stop) return mm_fail(MM_ERR_INVALID, "server is stopping");
   j->ticket = s->next_ticket++;
   s->jobs[j->ticket] = j;
-  s->queue.push_back(j);
+  s->queue[j->lane].push_back(j);
   *ticket = j->ticket;
   s->cv_sched.notify_all();
   return MM_OK;
@@ -214,14 +239,17 @@ extern "C" mm_status mm_server_destroy(mm_server* s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
-    for (auto& j : s->queue) {
-      j->status = MM_ERR_INVALID;
-      j->done = true;
+    for (auto& q : s->queue) {
+      for (auto& j : q) {
+        j->status = MM_ERR_INVALID;
+        j->done = true;
+      }
+      q.clear();
     }
-    s->queue.clear();
   }
   s->cv_sched.notify_all();
-  if (s->sched.joinable()) s->sched.join();
+  for (auto& t : s->sched)
+    if (t.joinable()) t.join();
   s->cv_done.notify_all();
   delete s;
   return MM_OK;

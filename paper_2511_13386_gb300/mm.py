@@ -75,9 +75,12 @@ class mm_tune_result(ctypes.Structure):
                 ("cand_ms", ctypes.c_double * 16)]
 
 
+MM_PARAREAL_RHO_LIFT, MM_PARAREAL_FULL_STATE = 0, 1
+
+
 class mm_parareal_cfg(ctypes.Structure):
     _fields_ = [("t_end", ctypes.c_double), ("n_slices", ctypes.c_int32),
-                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double)]
+                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("mode", ctypes.c_int32)]
 
 
 class mm_parareal_stats(ctypes.Structure):
@@ -276,8 +279,8 @@ def mm_lift(ctx: Ctx, batch: int, rho, g_out, stream=None):
 
 
 def parareal_run(ctx: Ctx, t_end: float, n_slices: int, max_iter: int, tol: float, rho0, g0,
-                 rho_slices_out, stream=None) -> dict:
-    cfg = mm_parareal_cfg(t_end, n_slices, max_iter, tol)
+                 rho_slices_out, stream=None, mode: int = MM_PARAREAL_RHO_LIFT) -> dict:
+    cfg = mm_parareal_cfg(t_end, n_slices, max_iter, tol, mode)
     st = mm_parareal_stats()
     _check(load().parareal_run(ctx.handle, ctypes.byref(cfg), _ptr(rho0), _ptr(g0),
                                _ptr(rho_slices_out), ctypes.byref(st), _stream(stream)))
@@ -323,8 +326,8 @@ def mm_batch_create() -> Batch:
 
 
 def mm_batch_add(batch: Batch, params: mm_params, t_end: float, n_slices: int, max_iter: int, tol: float,
-                 rho0, g0) -> int:
-    cfg = mm_parareal_cfg(t_end, n_slices, max_iter, tol)
+                 rho0, g0, mode: int = MM_PARAREAL_RHO_LIFT) -> int:
+    cfg = mm_parareal_cfg(t_end, n_slices, max_iter, tol, mode)
     i = ctypes.c_uint64()
     _check(load().mm_batch_add(batch.handle, ctypes.byref(params), ctypes.byref(cfg), _ptr(rho0), _ptr(g0),
                                ctypes.byref(i)))

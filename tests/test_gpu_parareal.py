@@ -148,3 +148,45 @@ def test_parareal_paper_setup(eps, L):
         sens = max(sens, rel(o2, ref))
     assert rel(got, ref) <= max(FP64_TOL, 20 * sens), (rel(got, ref), sens)
     assert info["mass_drift"] <= 1e-12
+
+
+@pytest.mark.parametrize("prec,L", [(mm.MM_FP64, 1), (mm.MM_FP64, 3), (mm.MM_FP32G, 1)])
+def test_full_state_parareal(prec, L):
+    """MM_PARAREAL_FULL_STATE: the slices carry (rho, g); against the
+    oracle's full-state Algorithm 1 after 2 iterations, and at K = N the
+    plain sequential F (no relifting) within the parity tolerance."""
+    dev = device()
+    w = W.batched(nx=128, nv=32, eps=1e-2, n_slices=4)
+    p = params(w.nx, w.nv, w.eps, prec, rho_bar=1.0, lift_order=L)
+    ctx = mm.mm_create(p)
+    w.t_end = 4 * 30 * mm.mm_query(ctx, 1.0)["dt_limit"]
+    gdt = gdtype(prec)
+    outs = {}
+    for K in (2, 4):
+        out = torch.empty((w.n_slices + 1, w.nx), dtype=torch.float64, device=dev)
+        info = mm.parareal_run(ctx, w.t_end, w.n_slices, K, 0.0, torch.tensor(w.rho0, device=dev),
+                               torch.tensor(w.g0, device=dev, dtype=gdt), out, mode=mm.MM_PARAREAL_FULL_STATE)
+        assert info["iterations"] == K
+        outs[K] = out.cpu().numpy()
+    ctx.close()
+    op = oparams(p)
+    tol = FP64_TOL if prec == mm.MM_FP64 else FP32_TOL
+    ref, err, it = O.parareal(op, w.rho0, w.g0, w.t_end, w.n_slices, 2, lift_order=L, mode=1)
+    assert rel(outs[2], ref) <= tol, rel(outs[2], ref)
+    plain = O.sequential(op, w.rho0, w.g0, w.t_end, w.n_slices, mode=1)
+    assert rel(outs[4], plain) <= tol, rel(outs[4], plain)
+    # the density mode reaches the relifted sequence, a different one
+    seq = O.sequential(op, w.rho0, w.g0, w.t_end, w.n_slices, lift_order=L)
+    assert rel(seq, plain) > 100 * tol
+
+
+def test_batch_rejects_full_state():
+    device()
+    w = W.small()
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP32G, rho_bar=1.0)
+    b = mm.mm_batch_create()
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_batch_add(b, p, w.t_end, w.n_slices, 2, 0.0, np.ascontiguousarray(w.rho0),
+                        np.ascontiguousarray(w.g0.astype(np.float32)), mode=mm.MM_PARAREAL_FULL_STATE)
+    assert e.value.status == mm.MM_ERR_INVALID
+    b.close()

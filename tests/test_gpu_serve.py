@@ -7,7 +7,7 @@ import time
 import numpy as np
 import pytest
 
-from paper_2511_13386_gb300 import mm
+from paper_2511_13386_gb300 import mm, workloads as W
 from tests.gpu_helpers import device
 from tests.test_gpu_batch import _host_g0, _mixed_set, _run_batch
 
@@ -83,3 +83,34 @@ def test_serving_rejections_and_per_request_failures():
     assert rb["status"] == mm.MM_ERR_INVALID
     assert rg["status"] == mm.MM_OK
     assert np.array_equal(rg["rho_T"], _run_batch([(p, w, t_end, N, K)])[0][0][-1])
+
+
+def _long_request():
+    """A solve whose parareal iteration costs ~2.7e10 fine cell-updates
+    (above the server's long-lane threshold of 2e10): Nx=2048, Nv=64,
+    N=32 slices of 6,400 steps, FP32, one iteration."""
+    nx, nv, N = 2048, 64, 32
+    w = W.batched(nx, nv, 1e-2, seed=W.SEED_BASE + 977, n_slices=N)
+    p = mm.mm_params_default(nx=nx, nv=nv, eps=1e-2, precision=mm.MM_FP32G, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    return (p, w, N * 6400 * dt * (1 - 1e-9), N, 1)
+
+
+def test_short_requests_do_not_wait_behind_a_long_one():
+    """Two lanes: the long request (submitted first) runs on most of the
+    SMs while the short ones run beside it on the SMs kept for them, so all
+    short requests complete before the long one; every result equals its
+    solo run."""
+    device()
+    long_req = _long_request()
+    shorts = _mixed_set()
+    solves = [long_req] + shorts
+    res = _serve(solves, budget=1 << 40, slots=64)
+    assert all(r["status"] == mm.MM_OK for r in res)
+    lat = [r["latency_ns"] for r in res]
+    assert max(lat[1:]) < lat[0], lat
+    solo = [_run_batch([s])[0][0][-1] for s in solves]
+    for q, r in enumerate(res):
+        assert np.array_equal(r["rho_T"], solo[q]), q
