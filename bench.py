@@ -117,11 +117,10 @@ def kernel_only(a):
 
 PROFILES = {
     "resident": (os.path.join(ROOT, "profiles", "fine_resident_kernel__batched_nx1024_nv64_fp32.md"),
-                 ["paper_2511_13386_gb300/csrc/mm_fine_resident.cu", "paper_2511_13386_gb300/csrc/ff.cuh",
-                  "paper_2511_13386_gb300/csrc/mm_internal.h"]),
+                 ["paper_2511_13386_gb300/csrc/mm_fine_resident.cu", "paper_2511_13386_gb300/csrc/ff.cuh"]),
     "streaming": (os.path.join(ROOT, "profiles", "fine_kernel__hybrid_nx4096_nv128_fp32.md"),
                   ["paper_2511_13386_gb300/csrc/mm_fine.cu", "paper_2511_13386_gb300/csrc/ff.cuh",
-                   "paper_2511_13386_gb300/csrc/lift.cuh", "paper_2511_13386_gb300/csrc/mm_internal.h"]),
+                   "paper_2511_13386_gb300/csrc/lift.cuh"]),
 }
 
 

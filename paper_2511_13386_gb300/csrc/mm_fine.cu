@@ -464,10 +464,22 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     }
   }
   // scalar constants in the working precisions (converted once)
-  const G ga = (G)A.a, gb = (G)A.b, g_inv_dx = (G)A.inv_dx, g_inv_dv = (G)A.inv_dv;
-  const G g_kflux = (G)(A.dt_dx * A.inv_eps);    // dt/dx <xi g> / eps
-  const G g_fflux = (G)(-A.dt_dx * A.m2);        // dt/dx (-m2 J)
-  const R Rdx = M::c(A.dx), Rinv_nx = M::c(1.0 / nx);
+  // (the FP32 path takes the float copies rounded on the host: a constant
+  // the compiler rematerialises under register pressure then costs a
+  // parameter load, not a double-to-float conversion on the FP64 pipe)
+  constexpr bool F32 = sizeof(G) == 4;
+  const G ga = F32 ? (G)A.fa : (G)A.a, gb = F32 ? (G)A.fb : (G)A.b;
+  const G g_inv_dx = F32 ? (G)A.f_inv_dx : (G)A.inv_dx, g_inv_dv = F32 ? (G)A.f_inv_dv : (G)A.inv_dv;
+  const G g_kflux = F32 ? (G)A.f_kflux : (G)(A.dt_dx * A.inv_eps);  // dt/dx <xi g> / eps
+  const G g_fflux = F32 ? (G)A.f_fflux : (G)(-A.dt_dx * A.m2);      // dt/dx (-m2 J)
+  R Rdx, Rinv_nx;
+  if constexpr (F32) {
+    Rdx = ff{A.f_dx, A.f_dx_lo};
+    Rinv_nx = ff{A.f_inv_nx, A.f_inv_nx_lo};
+  } else {
+    Rdx = A.dx;
+    Rinv_nx = 1.0 / nx;
+  }
 
   // ---- prologue: density, rho_bar, moments of g_in
   double rb = A.rho_bar;
@@ -481,6 +493,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     if (isnan(rb)) rb = block_sum_d(s, red) / nx;
   }
   const R Rrb = M::c(rb);
+  const float rb_f = (float)rb;  // the criteria's float combination
 
   // Sums of the lane partials of one interface column over each half of the
   // lane group (negative / positive velocities), by shuffles, with a
@@ -664,7 +677,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           jsum = ff_add_abs(jsum, J);
         }
         const float meanJ = block_sum_ff(jsum, red).hi * A.f_inv_nx;  // (syncs: Jc visible)
-        const float rbf = (float)rb;
+        const float rbf = rb_f;
         for (int c = tid; c < nx; c += T) {
           const ff J0 = Jf[c];
           const ff Jm1 = Jf[wrapi(c - 1, nx)], Jp1 = Jf[wrapi(c + 1, nx)];
@@ -800,13 +813,28 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       const int cl = wrapi(c - 1, nx), cr = wrapi(c + 1, nx);
       G* pr = C.par + 4 * c;
       const G e = pr[0];
-      const G J = M::flux_J(C.rho[c], C.rho[cr], e, g_inv_dx);
       const G ep = e > G(0) ? e : G(0), em = e < G(0) ? -e : G(0);
       const G pm = ((C.mp[c] - C.mp[cl]) - (C.mm[cr] - C.mm[c])) * g_inv_dx;
       const G* en = C.ends + 4 * c;
       const G gend = (G)0.5 * ((ep * en[2] - em * en[3]) - (ep * en[0] - em * en[1]));
       pr[2] = pm + gend;
-      pr[3] = J;
+      if constexpr (sizeof(G) == 4) {
+        // J in float-float: the fluid flux -m2 J feeds the density, and a
+        // float-rounded flux would leave cell-to-cell noise of ~1e-7 |F| in
+        // it, which the fourth derivative inside the remainder R amplifies
+        // by ~nx^4 (past the thresholds at nx >= 2048).  The sweep reads the
+        // high part (slot 3); the low part replaces the field's (slot 1,
+        // dead after the criteria).
+        const ff r0 = C.rho[c], r1 = C.rho[cr];
+        ff avg = ff_add_abs(r0, r1);
+        avg.hi *= 0.5f;
+        avg.lo *= 0.5f;
+        const ff J = ff_sub_abs(ff_mul_f(ff_sub_abs(r1, r0), g_inv_dx), ff_mul(ff{pr[0], pr[1]}, avg));
+        pr[3] = J.hi;
+        pr[1] = J.lo;
+      } else {
+        pr[3] = M::flux_J(C.rho[c], C.rho[cr], e, g_inv_dx);
+      }
     }
     __syncthreads();
     if constexpr (ADAPT) {
@@ -818,32 +846,40 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   // density update from the fluxes of the new g: one flux per interface
   // (kinetic: dt/dx <xi g>/eps, fluid: dt/dx (-m2 J)), or the cell-based
   // rule of S^HMM when flux_rule == 1.
-  auto flux_kin = [&](int c) { return C.fk[c]; };
+  // fluxes in the density's precision (float-float in the FP32 path): the
+  // kinetic flux of the last sweep, or the fluid flux dt/dx (-m2 J) from J
+  // (slot 3, and its low part in slot 1 in the FP32 path)
+  auto flux_kin = [&](int c) -> R {
+    if constexpr (sizeof(G) == 4) return ff{C.fk[c], 0.f};
+    else return C.fk[c];
+  };
+  auto flux_fluid = [&](int c) -> R {
+    if constexpr (sizeof(G) == 4) return ff_mul_f(ff{C.par[4 * c + 3], C.par[4 * c + 1]}, g_fflux);
+    else return g_fflux * C.par[4 * c + 3];
+  };
   auto is_kin = [&](int c) { return ADAPT ? kin_cur[c] != 0 : true; };
-  // J of an interface: slot 3 of its sweep constants
-  auto Jat = [&](int c) { return C.par[4 * c + 3]; };
   auto macro_C = [&]() {
     if (A.flux_rule == 0) {
       // each interface flux is evaluated by both of its cells, from the same
       // inputs, so the two evaluations are bitwise equal and mass telescopes
       for (int c = tid; c < nx; c += T) {
         const int cl = wrapi(c - 1, nx);
-        const G Fl = is_kin(cl) ? flux_kin(cl) : g_fflux * Jat(cl);
-        const G Fc = is_kin(c) ? flux_kin(c) : g_fflux * Jat(c);
-        C.rho[c] = M::addg(M::addg(C.rho[c], Fl), -Fc);
+        const R Fl = is_kin(cl) ? flux_kin(cl) : flux_fluid(cl);
+        const R Fc = is_kin(c) ? flux_kin(c) : flux_fluid(c);
+        C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fc);
       }
     } else {
       for (int c = tid; c < nx; c += T) {
         const int cl = wrapi(c - 1, nx);
-        G Fr, Fl;
+        R Fr, Fl;
         if (!ADAPT || cell_cur[c]) {
-          Fr = is_kin(c) ? flux_kin(c) : G(0);
-          Fl = is_kin(cl) ? flux_kin(cl) : G(0);
+          Fr = is_kin(c) ? flux_kin(c) : M::zero();
+          Fl = is_kin(cl) ? flux_kin(cl) : M::zero();
         } else {
-          Fr = g_fflux * Jat(c);
-          Fl = g_fflux * Jat(cl);
+          Fr = flux_fluid(c);
+          Fl = flux_fluid(cl);
         }
-        C.rho[c] = M::addg(M::addg(C.rho[c], Fl), -Fr);
+        C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fr);
       }
     }
   };
@@ -859,7 +895,8 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     int last = -10;
     auto col = [&](int i) { return src + (unsigned)(wrapi(i, nx) * nv + j0); };
     // one interface column: P = g(i-1), Cc = g(i), N = g(i+1), F = g(i+2)
-    // (in flight); afterwards P receives g(i+3).
+    // (in flight); afterwards P receives g(i+3).  (A five-column ring with
+    // two columns in flight measured no faster at the hybrid workload.)
     auto body = [&](int e, G(&P)[VPT], G(&Cc)[VPT], G(&N)[VPT], G(&F)[VPT]) {
       const bool valid = e < e1;
       const int i = valid ? (ADAPT ? C.list[e] : e) : last + 1;
