@@ -97,3 +97,39 @@ def test_hybrid_full_grid_window(prec, states):
             # the FP32 norms may decide a cell within float rounding of a
             # threshold the other way; anything beyond a handful is a bug
             assert (mo[b] != m_ref).sum() <= 4, (b, int((mo[b] != m_ref).sum()))
+
+
+def test_many_solve_batch_full_size_sampled():
+    """The many-solve workload at full size in the benchmark's launch
+    configuration: all 2,048 solves (Nx 128..8192, Nv 32..256, eps 1e-4..1,
+    N 16..256, adaptation on, FP32 g, 64 fine steps per slice) in one batch,
+    one parareal iteration.  Every solve finishes with finite densities and
+    its mass (Lemma 1); three of the cheapest solves are recomputed by the
+    oracle's Algorithm 1 (K = 1) and compared at the FP32 tolerance."""
+    device()
+    solves = W.many(2048, lazy=True)
+    b = mm.mm_batch_create()
+    ids, info = [], []
+    for w in solves:
+        w = W.materialise(w)
+        p = mm.mm_params_default(nx=w.nx, nv=w.nv, eps=w.eps, v_max=w.v_max, rho_bar=1.0, adapt=1,
+                                 thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, precision=mm.MM_FP32G)
+        ctx = mm.mm_create(p)
+        t_end = w.n_slices * 64 * mm.mm_query(ctx, 1.0)["dt_limit"] * (1 - 1e-9)
+        ctx.close()
+        ids.append(mm.mm_batch_add(b, p, t_end, w.n_slices, 1, 0.0, np.ascontiguousarray(w.rho0),
+                                   np.ascontiguousarray(w.g0.astype(np.float32))))
+        info.append((w, p, t_end, w.nx * w.nv * w.n_slices))
+    assert mm.mm_batch_step(b) == len(solves)
+    cheapest = sorted(range(len(solves)), key=lambda q: info[q][3])[:3]
+    for q, (w, p, t_end, _) in enumerate(info):
+        assert mm.mm_batch_query(b, ids[q])
+        out = np.empty((w.n_slices + 1, w.nx))
+        mm.mm_batch_take(b, ids[q], out)
+        assert np.isfinite(out).all(), q
+        m = out.sum(axis=1)
+        assert np.abs(m - m[0]).max() <= 1e-12 * abs(m[0]), q
+        if q in cheapest:
+            ref, _, _ = O.parareal(oparams(p), w.rho0, w.g0, t_end, w.n_slices, 1)
+            assert rel(out, ref) <= FP32_TOL, (q, rel(out, ref))
+    b.close()
