@@ -335,9 +335,11 @@ def run_ours(a, rank, world, dist):
            "h2d_bytes_per_step": int(rho0_h.nbytes + g0_h.nbytes),
            "d2h_bytes_per_step": int(out_h.nbytes)}
 
-    # roofline of the dominant kernel (the fine propagator)
-    fine_launch_ms = fine_ms / max(fine_n, 1)
-    upd_per_launch = updates_per_step  # one fine launch per step (K=1)
+    # roofline of the dominant kernel (the fine propagator): per F call of
+    # the step (K = 1: one call of all slices, which the resident kernel
+    # runs as one launch or as rounds of step chunks)
+    fine_launch_ms = fine_ms / a.steps
+    upd_per_launch = updates_per_step
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -356,6 +358,7 @@ def run_ours(a, rank, world, dist):
                 "traffic": profiled_traffic() if q["fine_kernel"] == 2 else None,
                 "peak_source": f"FP32 FMA lanes x clock: {n_sm} SMs x 128 x 2 x {sm_mhz:.0f} MHz",
                 "kernel": kname, "launch_ms": round(fine_launch_ms, 3),
+                "launches_per_call": round(fine_n / a.steps, 2),
                 "hbm_equivalent": {"achieved_gbs": round(alg_gbs, 1), "peak_gbs": hbm_peak,
                                    "frac_of_measured": round(alg_gbs / hbm_peak, 3)}}
     ctx.close()
@@ -805,8 +808,9 @@ def main():
             "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": None, "clocks": r["clocks"],
         }
-        # kernels per step: coarse chain, lift, fine, correction (K=1)
-        line["gpu_launches"] = 4 * a.steps
+        # kernels per step: coarse chain, lift, correction (K=1) and the
+        # fine propagator's launches
+        line["gpu_launches"] = 3 * a.steps + r["fine_launches"]
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -159,6 +159,9 @@ typedef struct {
   int64_t full_updates;      /* nx * nv * steps * batch */
   int32_t device_status;     /* mm_status reported by the kernels */
   double elapsed_ms;         /* device time of the call (events) */
+  int32_t launches;          /* kernel launches of the call: a batch of more
+                                states than the GPU holds at once runs the
+                                resident kernel in rounds of step chunks */
 } mm_fine_stats;
 
 /* Fill *p with defaults: x_len 1, v_max 8, eps 1, rho_bar NaN, adapt 0,
@@ -320,7 +323,7 @@ typedef struct {
   int64_t kinetic_updates;   /* summed over all fine propagations */
   double elapsed_ms;         /* device time of the whole call (events) */
   double fine_ms;            /* device time of the fine-propagator launches */
-  int32_t fine_launches;     /* fine-propagator launches */
+  int32_t fine_launches;     /* fine-propagator kernel launches */
 } mm_parareal_stats;
 
 /* Algorithm 1 (Sec. 3.3) with F = S^HMM, G = S^0 and the lifting of order

@@ -506,7 +506,8 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
     cudaEventRecord(e0, s);
   }
   const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
-  cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s)
+  int launches = 1;
+  cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s, &launches)
                         : mmk::launch_fine(a, fc.lay.vpt, fp32, smem, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
   if (stats) cudaEventRecord(e1, s);
@@ -532,6 +533,7 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
       stats->full_updates = (int64_t)n * batch * p.nx * p.nv;
       stats->device_status = hs[0];
       stats->elapsed_ms = ms;
+      stats->launches = launches;
     }
     if (hs[0] != 0) return mm_fail((mm_status)hs[0], "fine: non-finite density");
   }
@@ -854,7 +856,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     if (stats) {
       kin_total += fs.kinetic_updates;
       fine_ms += fs.elapsed_ms;
-      ++fine_launches;
+      fine_launches += fs.launches;
     }
     // sequential correction on the device (the coarse values before it are
     // kept for the full-state g correction)

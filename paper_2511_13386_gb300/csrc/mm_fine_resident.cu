@@ -42,6 +42,9 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "ff.cuh"
 #include "mm_internal.h"
 
@@ -136,7 +139,13 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   const int nx = A.nx, nv = A.nv;
   const int n = nx / C;                  // cells (and interfaces) of this CTA
   const int r = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int st = blockIdx.x / C;         // state
+  // work item of this cluster: a chunk of A.n_steps steps of one state
+  // (items are numbered chunk-major, item = chunk x batch + state, so a
+  // launch never holds two chunks of a state and its states wrap around the
+  // batch at most once); the first chunk of a state reads the input
+  const int item = A.res_item0 + (int)(blockIdx.x / C);
+  const bool from_input = A.res_from_input && item < A.batch;
+  const int stx = A.res_state0 + (int)(blockIdx.x / C);  // state, before the wrap
   const int a = r * n;                   // first global cell of this CTA
   const int rl = (r + C - 1) % C, rr = (r + 1) % C;
   const int nwc = n >> 5;                // warps that own cells
@@ -215,8 +224,11 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   };
 
   // ------------------------------------------------------------ entry ---
-  const size_t sbase = (size_t)st * nx;
-  const float* gin = reinterpret_cast<const float*>(A.g_in) + sbase * nv;
+  const size_t sbase = (size_t)(stx >= A.batch ? stx - A.batch : stx) * nx;
+  // chunk 0 starts from the input; later chunks from the previous chunk's
+  // output, which they overwrite in place (the whole state is in shared
+  // memory before the first write)
+  const float* gin = reinterpret_cast<const float*>(from_input ? A.g_in : A.g_buf0) + sbase * nv;
   // own columns, and (cluster) the two neighbour columns of step 0
   for (int i = grp; i < n; i += NGRP) {
     const float* s = gin + (size_t)(a + i) * nv + VPT * lig;
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   }
 
   // density, rho_bar and the entry field (prefix sum in double)
-  const double* rin = A.rho_in + sbase;
+  const double* rin = (from_input ? A.rho_in : A.rho_out) + sbase;
   const double rc = has_cell ? rin[a + tid] : 0.0;
   double rb = A.rho_bar;
   if (isnan(rb)) {
@@ -551,8 +563,81 @@ size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, 
   return bytes <= 232448u ? bytes : 0;
 }
 
+// Clusters of the resident kernel that the GPU holds at once for this
+// launch shape (the occupancy calculator's answer, cached per shape).
 template <int LG>
-static cudaError_t launch_res(const FineArgs& a, int C, size_t smem, cudaStream_t s) {
+static int resident_slots(int C, size_t smem) {
+  static std::mutex mu;
+  static int dev_c[4] = {-1, -1, -1, -1}, slots_c[4] = {0, 0, 0, 0};
+  static size_t smem_c[4] = {0, 0, 0, 0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int ci = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev_c[ci] == dev && smem_c[ci] == smem) return slots_c[ci];
+  int slots = 0;
+  if (C == 1) {
+    int per_sm = 0, n_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fine_resident_kernel<LG>, T, smem) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      slots = per_sm * n_sm;
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&slots, fine_resident_kernel<LG>, &cfg) != cudaSuccess) slots = 0;
+  }
+  cudaGetLastError();  // a failed query leaves no sticky error; chunking is then off
+  dev_c[ci] = dev;
+  smem_c[ci] = smem;
+  slots_c[ci] = slots;
+  return slots;
+}
+
+// Chunks per state of the step range.  With more states than the GPU holds
+// at once (Q clusters), one launch of all states runs in ceil(batch / Q)
+// waves and the last wave leaves SMs idle (128 states on 74 slots: 2 waves
+// for 1.73 waves of work).  Splitting every state's n steps into c chunks of
+// n / c steps and running the batch x c items in rounds of Q (chunk-major,
+// so a round never holds two chunks of one state and chunk k + 1 of a state
+// runs in a later round than chunk k) balances the SMs at the cost of one
+// entry and exit per chunk (the state goes through L2 between rounds); the
+// n mod c steps left over run as one more chunk of every state.  Every
+// launch then has one step count for all its clusters.  Cost model: rounds x
+// (chunk + kChunkEntry step-equivalents); ties go to fewer chunks.
+constexpr double kChunkEntry = 8.0;
+static double rounds_cost(int batch, int64_t n_steps, int slots, int c) {
+  const int64_t L = n_steps / c, r = n_steps % c;
+  const int64_t rounds = ((int64_t)batch * c + slots - 1) / slots;
+  double cost = (double)rounds * ((double)L + kChunkEntry);
+  if (r) cost += (double)((batch + slots - 1) / slots) * ((double)r + kChunkEntry);
+  return cost;
+}
+static int resident_chunks(int batch, int64_t n_steps, int slots) {
+  if (slots <= 0 || batch <= slots) return 1;
+  int best = 1;
+  double best_cost = rounds_cost(batch, n_steps, slots, 1);
+  const int cmax = (int)std::min<int64_t>(n_steps, 512);
+  for (int c = 2; c <= cmax; ++c) {
+    const double q = rounds_cost(batch, n_steps, slots, c);
+    if (q < 0.99 * best_cost) {
+      best = c;
+      best_cost = q;
+    }
+  }
+  return best;
+}
+
+template <int LG>
+static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG>,
@@ -560,30 +645,50 @@ static cudaError_t launch_res(const FineArgs& a, int C, size_t smem, cudaStream_
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(a.batch * C);
-  cfg.blockDim = dim3(T);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = C > 1 ? 1 : 0;  // C == 1: a plain launch
-  return cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG>, a, C);
+  const int slots = resident_slots<LG>(C, smem);
+  const int chunks = resident_chunks(a.batch, a.n_steps, slots);
+  const int64_t n_total = a.n_steps, L = n_total / chunks, r = n_total % chunks;
+  if (launches) *launches = 0;
+  // pass 0: chunks of L steps (chunk 0 from the input); pass 1: the r left over
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t items = pass == 0 ? (int64_t)a.batch * chunks : (r ? a.batch : 0);
+    if (items == 0) continue;
+    // a round holds at most one chunk of each state
+    const int64_t per_round = (pass == 0 && chunks == 1) ? items : std::min<int64_t>(slots, a.batch);
+    a.n_steps = pass == 0 ? L : r;
+    a.res_from_input = pass == 0 ? 1 : 0;
+    for (int64_t i0 = 0; i0 < items; i0 += per_round) {
+      a.res_item0 = (int)i0;
+      a.res_state0 = (int)(i0 % a.batch);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(std::min<int64_t>(per_round, items - i0) * C));
+      cfg.blockDim = dim3(T);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = C > 1 ? 1 : 0;  // C == 1: a plain launch
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG>, (const FineArgs)a, C);
+      if (e != cudaSuccess) return e;
+      if (launches) ++*launches;
+    }
+  }
+  return cudaSuccess;
 }
 
-cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s) {
+cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s, int* launches) {
   FineArgs a = args;
   fine_args_floats(a);
   switch (a.nv / VPT) {
-    case 2: return launch_res<2>(a, C, smem, s);
-    case 4: return launch_res<4>(a, C, smem, s);
-    case 8: return launch_res<8>(a, C, smem, s);
-    case 16: return launch_res<16>(a, C, smem, s);
-    case 32: return launch_res<32>(a, C, smem, s);
+    case 2: return launch_res<2>(a, C, smem, s, launches);
+    case 4: return launch_res<4>(a, C, smem, s, launches);
+    case 8: return launch_res<8>(a, C, smem, s, launches);
+    case 16: return launch_res<16>(a, C, smem, s, launches);
+    case 32: return launch_res<32>(a, C, smem, s, launches);
   }
   return cudaErrorInvalidValue;
 }

@@ -62,6 +62,11 @@ struct FineArgs {
   double xiM;                  // <xi M> of the discrete Maxwellian (lifting)
   double mu3;                  // <xi^3 M> (lifting of order three)
   int lift_order;              // order L of the lifting (Def. 1), 1..3
+  // resident kernel: first work item of this launch, and whether the
+  // launch's first chunk of each state reads the input (set by
+  // launch_fine_resident)
+  int res_item0, res_from_input;
+  int res_state0;               // res_item0 mod batch
 };
 
 // Work list of fine propagations across solves (persistent kernel).
@@ -123,7 +128,9 @@ cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem,
 // cluster size (0: shape not supported) and the dynamic shared memory.
 int fine_resident_cluster(int nx, int nv, bool fp32, bool adapt, int flux_rule, size_t* smem);
 size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, int C);
-cudaError_t launch_fine_resident(const FineArgs& a, int C, size_t smem, cudaStream_t s);
+// *launches (nullable) receives the kernel launches made: a batch larger
+// than the GPU holds at once runs in rounds.
+cudaError_t launch_fine_resident(const FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches = nullptr);
 
 // Arguments of the macroscopic kernels (coarse step, lift, correction).
 struct MacroArgs {

@@ -140,6 +140,7 @@ extern "C" mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, doubl
     stats->full_updates = f.n_steps * (int64_t)batch * a.nx * a.nv;
     stats->device_status = hs[0];
     stats->elapsed_ms = 0.0;
+    stats->launches = 1;
     if (hs[0] != 0) return mm_fail((mm_status)hs[0], "fine: non-finite density");
   }
   return MM_OK;

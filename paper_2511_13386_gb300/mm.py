@@ -64,7 +64,7 @@ class mm_info(ctypes.Structure):
 class mm_fine_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("kinetic_updates", ctypes.c_int64),
                 ("full_updates", ctypes.c_int64), ("device_status", ctypes.c_int32),
-                ("elapsed_ms", ctypes.c_double)]
+                ("elapsed_ms", ctypes.c_double), ("launches", ctypes.c_int32)]
 
 
 class mm_tune_result(ctypes.Structure):

@@ -123,3 +123,57 @@ def test_resident_rejects_unsupported_options():
         with pytest.raises(mm.MMError) as e:
             mm.mm_create(p)
         assert e.value.status == mm.MM_ERR_INVALID
+
+
+def _rounds_case(rho_bar):
+    """640 states of Nx=256, Nv=32 (one CTA each, two per SM): more states
+    than the GPU holds at once, over enough steps that the launch runs in
+    rounds of step chunks."""
+    nx, nv, B, steps = 256, 32, 640, 380
+    w, rho, g = _state(nx, nv, 8, seed=23)
+    rho = np.tile(rho, (B // 8, 1)) * (1.0 + 0.01 * np.arange(B))[:, None]
+    g = np.tile(g, (B // 8, 1, 1))
+    p = params(nx, nv, w.eps, mm.MM_FP32G, rho_bar=rho_bar, fine_kernel=2)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    return p, rho, g, steps * dt * (1 - 1e-9), steps
+
+
+@pytest.mark.parametrize("rho_bar", [1.0, float("nan")], ids=["fixed", "input-mean"])
+def test_resident_rounds_of_step_chunks(rho_bar):
+    """States in every round and chunk position match the oracle; every
+    state conserves mass; the kinetic-update count covers every chunk."""
+    p, rho, g, span, steps = _rounds_case(rho_bar)
+    ro, go, mo, st, q = run_fine(p, rho, g, span)
+    B, nx, nv = rho.shape[0], p.nx, p.nv
+    assert q["n_steps"] == steps and st["device_status"] == 0
+    assert st["launches"] > 1, st
+    assert st["kinetic_updates"] == B * steps * nx * nv
+    assert (mo == 1).all()
+    assert np.abs(ro.sum(axis=1) - rho.sum(axis=1)).max() / rho.sum(axis=1).max() <= 1e-12
+    for b in (0, 151, 303, 304, 455, 607, 639):
+        op = oparams(p)
+        if np.isnan(rho_bar):
+            op.rho_bar = float(rho[b].mean())
+        r_ref, g_ref, _, _ = O.fine(op, q["n_steps"], q["dt"], rho[b], g[b])
+        assert rel(ro[b], r_ref) <= FP32_TOL, (b, rel(ro[b], r_ref))
+        assert rel(go[b], g_ref) <= 1e-3, (b, rel(go[b], g_ref))
+
+
+def test_resident_rounds_in_place():
+    """Rounds with the outputs aliasing the inputs give the same bits as
+    with separate outputs."""
+    torch = pytest.importorskip("torch")
+    from tests.gpu_helpers import device
+    dev = device()
+    p, rho, g, span, _ = _rounds_case(1.0)
+    ctx = mm.mm_create(p)
+    r = torch.tensor(rho, device=dev)
+    gg = torch.tensor(g, device=dev, dtype=torch.float32)
+    ro, go = torch.empty_like(r), torch.empty_like(gg)
+    st = mm.mm_fine_propagate(ctx, rho.shape[0], span, r, gg, ro, go, stats=True)
+    assert st["launches"] > 1
+    mm.mm_fine_propagate(ctx, rho.shape[0], span, r, gg, r, gg)
+    ctx.close()
+    assert torch.equal(r, ro) and torch.equal(gg, go)
