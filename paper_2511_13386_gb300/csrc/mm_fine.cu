@@ -133,6 +133,7 @@ enum ColField {
             //   phase) and the write list (compaction to the end of the
             //   sweep) share it: the three lifetimes are disjoint
   F_ENDS,   // G [nx][4]: g at the two lowest and the two highest nodes
+  F_ELO,    // float [nx]: low part of the float-float field (FP32 path)
   F_S,      // R [nx]: prefix sums of the Poisson law (without adaptation)
   F_COUNT
 };
@@ -168,6 +169,7 @@ __host__ __device__ inline ColLayout col_layout(int nx, int gbytes, bool adapt, 
   sz[F_N2] = a * gbytes * n;
   sz[F_JD] = a * 8 * n;
   sz[F_ENDS] = gbytes * 4 * n;
+  sz[F_ELO] = (gbytes == 4 ? 4 : 0) * n;
   sz[F_S] = (1 - a) * 8 * n;
   ColLayout L;
   L.smem_mask = 0;
@@ -290,6 +292,7 @@ struct Cols {
   using R = typename MP<G>::R;
   R *rho, *S, *base;
   G *fk, *mp, *mm, *n2, *ends, *par;
+  float* elo;
   uint16_t* list;
   double* jd;
   uint8_t *cell0, *cell1, *kin0, *kin1, *kin2;
@@ -311,6 +314,7 @@ __device__ __forceinline__ Cols<G> carve(unsigned char* sbase, unsigned char* gb
   c.n2 = reinterpret_cast<G*>(at(F_N2));
   c.ends = reinterpret_cast<G*>(at(F_ENDS));
   c.par = reinterpret_cast<G*>(at(F_PAR));
+  c.elo = reinterpret_cast<float*>(at(F_ELO));
   c.list = reinterpret_cast<uint16_t*>(at(F_JD));
   c.jd = reinterpret_cast<double*>(at(F_JD));
   c.cell0 = at(F_CELL0);
@@ -577,70 +581,73 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
 
   // ------------------------------------------------------------ macro A --
   // E, J, criteria/status, write list and sweep constants for step n.
-  auto macro_A = [&](bool initial) {
+  auto macro_A = [&](bool initial, bool prefix) {
     // the density was last written with interleaved ownership (macro_C or
     // the prologue); the first Poisson pass reads it in contiguous chunks
     __syncthreads();
     if constexpr (ADAPT) {
       if (tid == 0) rint[1] = 0;  // kinetic-interface count of this step
     }
-    // Poisson law: S_c = sum_{m<=c} (rho_m - rho_bar) dx ; E = S - mean(S),
-    // with mean(S) = sum_m (nx - m) d_m / nx.
-    R t1 = M::zero(), t2 = M::zero();
-    G wgt = G(nx - c0);  // nx - c, counted down without an int conversion
-    for (int c = c0; c < c1; ++c) {
-      const R d = M::mul(M::sub(C.rho[c], Rrb), Rdx);
-      t1 = M::add(t1, d);
-      C.S[c] = t1;
-      t2 = M::add(t2, M::mulg(d, wgt));
-      wgt -= G(1);
-    }
-    R inc = t1;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const R t = M::shfl_up(inc, d);
-      if (l >= d) inc = M::add(inc, t);
-    }
-    R ex_lane = M::shfl_up(inc, 1);
-    if (l == 0) ex_lane = M::zero();
-    R ws = t2;
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) ws = M::add(ws, M::shfl_xor(ws, m));
-    R* rr = reinterpret_cast<R*>(red);
-    if (l == 31) rr[w] = inc;
-    if (l == 0) rr[32 + w] = ws;
-    __syncthreads();
-    if (w == 0) {  // exclusive scan of the warp totals and the mean, once
-      constexpr int NW = T / 32;
-      R v = l < NW ? rr[l] : M::zero();
-      R u = l < NW ? rr[32 + l] : M::zero();
-#pragma unroll
-      for (int d = 1; d < NW; d <<= 1) {
-        const R t = M::shfl_up(v, d);
-        if (l >= d) v = M::add(v, t);
+    if (prefix) {  // else E^n was advanced by the Ampere identity in macro_C
+      // Poisson law: S_c = sum_{m<=c} (rho_m - rho_bar) dx ; E = S - mean(S),
+      // with mean(S) = sum_m (nx - m) d_m / nx.
+      R t1 = M::zero(), t2 = M::zero();
+      G wgt = G(nx - c0);  // nx - c, counted down without an int conversion
+      for (int c = c0; c < c1; ++c) {
+        const R d = M::mul(M::sub(C.rho[c], Rrb), Rdx);
+        t1 = M::add(t1, d);
+        C.S[c] = t1;
+        t2 = M::add(t2, M::mulg(d, wgt));
+        wgt -= G(1);
       }
+      R inc = t1;
 #pragma unroll
-      for (int m = NW / 2; m > 0; m >>= 1) u = M::add(u, M::shfl_xor(u, m));
-      R ex = M::shfl_up(v, 1);
-      if (l == 0) ex = M::zero();
-      if (l < NW) rr[64 + l] = ex;
-      if (l == 0) rr[96] = M::mul(u, Rinv_nx);
-    }
-    __syncthreads();
-    C.base[tid] = M::add(rr[64 + w], ex_lane);   // prefix before this thread's chunk
-    const R meanS = rr[96];
-    __syncthreads();
-    for (int c = tid; c < nx; c += T) {  // E^n into slots 0, 1 of the sweep constants
-      const R E = M::sub(M::add(C.base[c >> lcpt], C.S[c]), meanS);
-      if constexpr (sizeof(G) == 4) {
-        *reinterpret_cast<ff*>(C.par + 4 * c) = E;
-      } else {
-        C.par[4 * c] = E;
-        C.par[4 * c + 1] = 0.0;
-        if constexpr (ADAPT) C.par[4 * c + 2] = C.rho[c];  // density copy for the criteria
+      for (int d = 1; d < 32; d <<= 1) {
+        const R t = M::shfl_up(inc, d);
+        if (l >= d) inc = M::add(inc, t);
       }
+      R ex_lane = M::shfl_up(inc, 1);
+      if (l == 0) ex_lane = M::zero();
+      R ws = t2;
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) ws = M::add(ws, M::shfl_xor(ws, m));
+      R* rr = reinterpret_cast<R*>(red);
+      if (l == 31) rr[w] = inc;
+      if (l == 0) rr[32 + w] = ws;
+      __syncthreads();
+      if (w == 0) {  // exclusive scan of the warp totals and the mean, once
+        constexpr int NW = T / 32;
+        R v = l < NW ? rr[l] : M::zero();
+        R u = l < NW ? rr[32 + l] : M::zero();
+#pragma unroll
+        for (int d = 1; d < NW; d <<= 1) {
+          const R t = M::shfl_up(v, d);
+          if (l >= d) v = M::add(v, t);
+        }
+#pragma unroll
+        for (int m = NW / 2; m > 0; m >>= 1) u = M::add(u, M::shfl_xor(u, m));
+        R ex = M::shfl_up(v, 1);
+        if (l == 0) ex = M::zero();
+        if (l < NW) rr[64 + l] = ex;
+        if (l == 0) rr[96] = M::mul(u, Rinv_nx);
+      }
+      __syncthreads();
+      C.base[tid] = M::add(rr[64 + w], ex_lane);   // prefix before this thread's chunk
+      const R meanS = rr[96];
+      __syncthreads();
+      for (int c = tid; c < nx; c += T) {  // E^n into slot 0 of the sweep constants (+ low part)
+        const R E = M::sub(M::add(C.base[c >> lcpt], C.S[c]), meanS);
+        if constexpr (sizeof(G) == 4) {
+          C.par[4 * c] = E.hi;
+          C.elo[c] = E.lo;
+        } else {
+          C.par[4 * c] = E;
+          C.par[4 * c + 1] = 0.0;
+          if constexpr (ADAPT) C.par[4 * c + 2] = C.rho[c];  // density copy for the criteria
+        }
+      }
+      __syncthreads();  // rho final for this step; E of all cells visible
     }
-    __syncthreads();  // rho final for this step; E of all cells visible
 
     if constexpr (ADAPT) {
       // criteria of Sec. 2.2 and status update of Sec. 2.3: the remainder R
@@ -658,7 +665,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         // D2 f = (270 s1 - 27 s2 + 2 s3 - 490 f0) / 180,
         // D3 f = (-13 e1 + 8 e2 - e3) / 8, with e_k = f_{+k} - f_{-k},
         // s_k = f_{+k} + f_{-k} (then divided by dx^d).
-        auto Ef = [&](int c) { return *reinterpret_cast<const ff*>(C.par + 4 * c); };
+        auto Ef = [&](int c) { return ff{C.par[4 * c], C.elo[c]}; };
         ff* Jf = reinterpret_cast<ff*>(C.jd);
         const ff k1 = {A.f_k1, A.f_k1_lo};
         auto rho_f = [&](int c) { return C.rho[wrapi(c, nx)]; };
@@ -829,7 +836,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         ff avg = ff_add_abs(r0, r1);
         avg.hi *= 0.5f;
         avg.lo *= 0.5f;
-        const ff J = ff_sub_abs(ff_mul_f(ff_sub_abs(r1, r0), g_inv_dx), ff_mul(ff{pr[0], pr[1]}, avg));
+        const ff J = ff_sub_abs(ff_mul_f(ff_sub_abs(r1, r0), g_inv_dx), ff_mul(ff{pr[0], C.elo[c]}, avg));
         pr[3] = J.hi;
         pr[1] = J.lo;
       } else {
@@ -858,8 +865,39 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     else return g_fflux * C.par[4 * c + 3];
   };
   auto is_kin = [&](int c) { return ADAPT ? kin_cur[c] != 0 : true; };
+  // FP32 path with one flux per interface: the field is advanced with the
+  // density instead of re-solving the Poisson law at the next step.  Summing
+  // the density update over the cells m <= c telescopes the fluxes, so the
+  // law of S^MM at n+1 is exactly E^{n+1}_c = E^n_c - dx (F_c - mean F).
+  // Pass 1 forms every interface flux in float-float (high part over the
+  // kinetic flux, low part over the low part of J, both read only here);
+  // pass 2 updates the density and the field.
+  const bool ampere = F32 && A.flux_rule == 0;
+  auto macro_C_ampere = [&]() {
+    if constexpr (F32) {
+      ff fsum = {0.f, 0.f};
+      for (int c = tid; c < nx; c += T) {
+        const ff F = is_kin(c) ? flux_kin(c) : flux_fluid(c);
+        C.fk[c] = F.hi;
+        C.par[4 * c + 1] = F.lo;
+        fsum = ff_add_abs(fsum, F);
+      }
+      const ff Fbar = ff_mul(block_sum_ff(fsum, red), Rinv_nx);  // (syncs: fluxes visible)
+      const ff mdx = {-Rdx.hi, -Rdx.lo};
+      for (int c = tid; c < nx; c += T) {
+        const int cl = wrapi(c - 1, nx);
+        const ff Fl = {C.fk[cl], C.par[4 * cl + 1]}, Fc = {C.fk[c], C.par[4 * c + 1]};
+        C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fc);
+        const ff E = ff_add(ff{C.par[4 * c], C.elo[c]}, ff_mul(ff_sub(Fc, Fbar), mdx));
+        C.par[4 * c] = E.hi;
+        C.elo[c] = E.lo;
+      }
+    }
+  };
   auto macro_C = [&]() {
-    if (A.flux_rule == 0) {
+    if (ampere) {
+      macro_C_ampere();
+    } else if (A.flux_rule == 0) {
       // each interface flux is evaluated by both of its cells, from the same
       // inputs, so the two evaluations are bitwise equal and mass telescopes
       for (int c = tid; c < nx; c += T) {
@@ -969,7 +1007,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   };
 
   // ------------------------------------------------------------ step loop --
-  macro_A(true);
+  macro_A(true, true);
   const G* src = gin;
   for (int64_t s = 0; s < A.n_steps; ++s) {
     G* dst = ((A.n_steps - 1 - s) & 1) ? buf1 : buf0;
@@ -980,7 +1018,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       uint8_t* t = cell_cur; cell_cur = cell_nxt; cell_nxt = t;
       t = kin_prev2; kin_prev2 = kin_prev; kin_prev = kin_cur; kin_cur = t;
     }
-    if (s + 1 < A.n_steps) macro_A(false);
+    if (s + 1 < A.n_steps) macro_A(false, !ampere);
     src = dst;
   }
   __syncthreads();
