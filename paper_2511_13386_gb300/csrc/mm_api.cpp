@@ -105,6 +105,10 @@ struct mm_ctx {
   int tuned_kernel = 0;       // 1 streaming, 2 resident
   int tuned_cluster = 0;      // resident: CTAs per state
   mmk::LaneLayout tuned_lay;  // streaming: lane layout
+  // second stream and events of parareal_run's overlap of Algorithm 1's
+  // sequential parts with the resident kernel's rounds (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ov[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // ------------------------------------------------------- launch choice ---
@@ -354,6 +358,9 @@ void mmk::ctx_release(mm_ctx* c, cudaStream_t s) {
   if (!c) return;
   cudaSetDevice(c->device);
   c->ws.release_all(s);
+  for (cudaEvent_t& ev : c->ov)
+    if (ev) cudaEventDestroy(ev);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->d_vtab) cudaFreeAsync(c->d_vtab, s);
   if (c->d_vtab_f) cudaFreeAsync(c->d_vtab_f, s);
   delete c;
@@ -415,7 +422,8 @@ static mm_status device_view(mm_ctx* c, int slot, const void* p, size_t bytes, b
 
 static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const double* rho_in,
                            const void* g_in, double* rho_out, void* g_out, uint8_t* mask_out,
-                           double rho_bar, mm_fine_stats* stats, cudaStream_t s) {
+                           double rho_bar, mm_fine_stats* stats, cudaStream_t s,
+                           const mmk::ResHooks* hooks = nullptr) {
   const mm_params& p = c->p;
   const bool fp32 = p.precision == MM_FP32G;
   const size_t gsz = fp32 ? 4 : 8;
@@ -507,7 +515,7 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   }
   const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
   int launches = 1;
-  cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s, &launches)
+  cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s, &launches, hooks)
                         : mmk::launch_fine(a, fc.lay.vpt, fp32, smem, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
   if (stats) cudaEventRecord(e1, s);
@@ -821,9 +829,49 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   const size_t wsb = mmk::macro_ws_bytes(nx, std::max(N, 1));
   if (wsb && (st = c->ws.get(WS_MACRO, wsb, s, &gws)) != MM_OK) return st;
 
-  // coarse guess: rho^{n+1,0} = G(rho^{n,0})
-  cudaError_t e = mmk::launch_coarse_chain(ma, N, (double*)rho, (double*)gprev, (double*)gws, s);
-  if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
+  // Overlap of the sequential parts with the fine propagator (density mode,
+  // resident kernel in rounds, macro scratch in shared memory so that the
+  // two streams share no workspace): the coarse guess and lifting of the
+  // slices that the first round does not take run on a second stream during
+  // that round, and the correction of the slices whose last chunk has run
+  // runs on it during the last round.  The results are those of the
+  // sequential order: every dependency is an event.
+  const FineChoice fc = fine_choice(c);
+  const bool can_overlap = !full && fc.kernel == 2 && wsb == 0;
+  auto plan_for = [&](int batch) { return mmk::resident_plan(nv, batch, nf, fc.C, fc.res_smem); };
+  if (can_overlap && !c->side) {
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) c->side = nullptr;
+    for (cudaEvent_t& ev : c->ov)
+      if (!ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  }
+  const bool ov_ok = can_overlap && c->side && c->ov[0] && c->ov[1] && c->ov[2] && c->ov[3];
+  cudaStream_t side = c->side;
+
+  // coarse guess: rho^{n+1,0} = G(rho^{n,0}); with the overlap, slices
+  // 1..p-1 (the first round's states) first, the rest on the second stream
+  int p_split = 0;  // states of the first round, when the guess is split
+  if (ov_ok && N >= 3) {
+    const mmk::ResPlan q0 = plan_for(N);
+    if (q0.launches() >= 2 && q0.per_round0 >= 2 && q0.per_round0 < N) p_split = q0.per_round0;
+  }
+  cudaError_t e;
+  if (p_split) {
+    e = mmk::launch_coarse_chain(ma, p_split - 1, (double*)rho, (double*)gprev, (double*)gws, s);
+    if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
+    CK(cudaEventRecord(c->ov[0], s), "overlap event");
+    CK(cudaStreamWaitEvent(side, c->ov[0], 0), "overlap wait");
+    e = mmk::launch_coarse_chain(ma, N - p_split + 1, (double*)rho + (size_t)(p_split - 1) * nx,
+                                 (double*)gprev + (size_t)(p_split - 1) * nx, (double*)gws, side);
+    if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
+    mmk::MacroArgs la = macro_args(c, N - p_split, span, rb);
+    e = mmk::launch_lift(la, (const double*)rho + (size_t)p_split * nx, (char*)gb + (size_t)p_split * G1, fp32,
+                         (double*)gws, side);
+    if (e != cudaSuccess) return mm_cuda_fail(e, "lift");
+    CK(cudaEventRecord(c->ov[1], side), "overlap event");
+  } else {
+    e = mmk::launch_coarse_chain(ma, N, (double*)rho, (double*)gprev, (double*)gws, s);
+    if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
+  }
 
   int it = 0;
   int64_t kin_total = 0;
@@ -836,11 +884,18 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     // Density mode: g relifted from the density into gb[0..batch) (slice 0
     // from g0).  Full state: the slices' own g, kept at gb[n] (lifted once
     // from the coarse guess).
+    mmk::ResHooks hooks{};
+    bool use_hooks = false;
     if (k == 0) {
       CK(cudaMemcpyAsync(gb, g0, (size_t)nx * nv * gsz, cudaMemcpyDefault, s), "copy g0");
-      if (N > 1) {
-        mmk::MacroArgs la = macro_args(c, N - 1, span, rb);
+      const int n_lift = p_split ? p_split - 1 : N - 1;  // slices 1..n_lift here
+      if (n_lift > 0) {
+        mmk::MacroArgs la = macro_args(c, n_lift, span, rb);
         e = mmk::launch_lift(la, (const double*)rho + nx, (char*)gb + G1, fp32, (double*)gws, s);
+      }
+      if (p_split) {  // the second round needs the rest of the guess and its lifting
+        hooks.before[1] = c->ov[1];
+        use_hooks = true;
       }
     } else if (!full) {
       mmk::MacroArgs la = macro_args(c, batch, span, rb);
@@ -849,10 +904,27 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     if (e != cudaSuccess) return mm_cuda_fail(e, "lift");
     void* g_in = full ? (void*)((char*)gb + (size_t)k * G1) : gb;
     void* g_out = full ? (void*)((char*)gb2 + (size_t)(k + 1) * G1) : gb;  // full: F_g(U^{n,k}) at n+1
+    // correction split: the states final before the last launch (a prefix,
+    // the items being chunk-major) are corrected during it
+    int m_split = 0;
+    if (ov_ok) {
+      const mmk::ResPlan q = plan_for(batch);
+      const int j = q.launches() - 2;
+      if (j >= 0 && j < mmk::ResHooks::kMax) {
+        while (m_split < batch && q.final_launch(m_split) <= j) ++m_split;
+        if (m_split >= batch) m_split = 0;
+        if (m_split) {
+          hooks.after[j] = c->ov[2];
+          use_hooks = true;
+        }
+      }
+    }
     mm_fine_stats fs;
     st = fine_impl(c, batch, nf, dtf, (const double*)rho + (size_t)k * nx, g_in,
-                   (double*)frho + (size_t)(k + 1) * nx, g_out, nullptr, rb, stats ? &fs : nullptr, s);
+                   (double*)frho + (size_t)(k + 1) * nx, g_out, nullptr, rb, stats ? &fs : nullptr, s,
+                   use_hooks ? &hooks : nullptr);
     if (st != MM_OK) return st;
+    if (k == 0 && p_split && !use_hooks) CK(cudaStreamWaitEvent(s, c->ov[1], 0), "overlap join");
     if (stats) {
       kin_total += fs.kinetic_updates;
       fine_ms += fs.elapsed_ms;
@@ -869,6 +941,17 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     ca.frho = (const double*)frho;
     ca.gprev = (double*)gprev;
     ca.err = (double*)errp;
+    if (m_split) {  // slices k..k+m-1 on the second stream, then the rest
+      mmk::CorrectArgs c1 = ca;
+      c1.n_slices = k + m_split;
+      CK(cudaStreamWaitEvent(side, c->ov[2], 0), "overlap wait");
+      e = mmk::launch_correct(c1, (double*)gws, side);
+      if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
+      CK(cudaEventRecord(c->ov[3], side), "overlap event");
+      CK(cudaStreamWaitEvent(s, c->ov[3], 0), "overlap join");
+      ca.k = k + m_split;
+      ca.err = (double*)errp + 1;
+    }
     e = mmk::launch_correct(ca, (double*)gws, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
     if (full) {  // g^{n+1,k+1} = F_g(U^{n,k}) + (L G rho^{n,k+1} - L G rho^{n,k}), n = k..N-1
@@ -879,9 +962,10 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       if (e != cudaSuccess) return mm_cuda_fail(e, "full-state correction");
       std::swap(gb, gb2);
     }
-    double err = 0;
-    CK(cudaMemcpyAsync(&err, errp, 8, cudaMemcpyDeviceToHost, s), "read error");
+    double errs[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(errs, errp, m_split ? 16 : 8, cudaMemcpyDeviceToHost, s), "read error");
     CK(cudaStreamSynchronize(s), "parareal: synchronise");
+    const double err = std::max(errs[0], errs[1]);
     if (stats && k < 64) stats->err[k] = err;
     ++it;
     if (err < cfg->tol) break;

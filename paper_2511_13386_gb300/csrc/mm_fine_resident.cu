@@ -637,7 +637,7 @@ static int resident_chunks(int batch, int64_t n_steps, int slots) {
 }
 
 template <int LG>
-static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches) {
+static cudaError_t configure_res() {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG>,
@@ -645,19 +645,52 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int slots = resident_slots<LG>(C, smem);
-  const int chunks = resident_chunks(a.batch, a.n_steps, slots);
-  const int64_t n_total = a.n_steps, L = n_total / chunks, r = n_total % chunks;
+  return cudaSuccess;
+}
+
+// The launches one call makes: pass 0 runs batch x chunks items of L steps
+// in rounds of per_round0 (chunk 0 from the input), pass 1 the r steps left
+// over, batch items in rounds of per_round1.
+static ResPlan make_plan(int batch, int64_t n_steps, int slots) {
+  ResPlan q{};
+  q.chunks = resident_chunks(batch, n_steps, slots);
+  q.L = n_steps / q.chunks;
+  q.r = n_steps % q.chunks;
+  const int64_t items0 = (int64_t)batch * q.chunks;
+  // a round holds at most one chunk of each state
+  q.per_round0 = (int)(q.chunks == 1 ? items0 : std::min<int64_t>(slots, batch));
+  q.per_round1 = (int)std::min<int64_t>(slots > 0 ? slots : batch, batch);
+  q.launches0 = (int)((items0 + q.per_round0 - 1) / q.per_round0);
+  q.launches1 = q.r ? (batch + q.per_round1 - 1) / q.per_round1 : 0;
+  q.batch = batch;
+  return q;
+}
+
+int ResPlan::final_launch(int state) const {
+  if (r) return launches0 + state / per_round1;
+  return (int)(((int64_t)(chunks - 1) * batch + state) / per_round0);
+}
+
+template <int LG>
+static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches,
+                              const ResHooks* hooks) {
+  cudaError_t e0 = configure_res<LG>();
+  if (e0 != cudaSuccess) return e0;
+  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG>(C, smem));
+  const int64_t L = q.L, r = q.r;
   if (launches) *launches = 0;
-  // pass 0: chunks of L steps (chunk 0 from the input); pass 1: the r left over
+  int li = 0;  // launch index
   for (int pass = 0; pass < 2; ++pass) {
-    const int64_t items = pass == 0 ? (int64_t)a.batch * chunks : (r ? a.batch : 0);
+    const int64_t items = pass == 0 ? (int64_t)a.batch * q.chunks : (r ? a.batch : 0);
     if (items == 0) continue;
-    // a round holds at most one chunk of each state
-    const int64_t per_round = (pass == 0 && chunks == 1) ? items : std::min<int64_t>(slots, a.batch);
+    const int64_t per_round = pass == 0 ? q.per_round0 : q.per_round1;
     a.n_steps = pass == 0 ? L : r;
     a.res_from_input = pass == 0 ? 1 : 0;
-    for (int64_t i0 = 0; i0 < items; i0 += per_round) {
+    for (int64_t i0 = 0; i0 < items; i0 += per_round, ++li) {
+      if (hooks && li < ResHooks::kMax && hooks->before[li]) {
+        const cudaError_t ew = cudaStreamWaitEvent(s, hooks->before[li], 0);
+        if (ew != cudaSuccess) return ew;
+      }
       a.res_item0 = (int)i0;
       a.res_state0 = (int)(i0 % a.batch);
       cudaLaunchConfig_t cfg = {};
@@ -675,20 +708,37 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
       const cudaError_t e = cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG>, (const FineArgs)a, C);
       if (e != cudaSuccess) return e;
       if (launches) ++*launches;
+      if (hooks && li < ResHooks::kMax && hooks->after[li]) {
+        const cudaError_t er = cudaEventRecord(hooks->after[li], s);
+        if (er != cudaSuccess) return er;
+      }
     }
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s, int* launches) {
+ResPlan resident_plan(int nv, int batch, int64_t n_steps, int C, size_t smem) {
+  int slots = 0;
+  switch (nv / VPT) {
+    case 2: if (configure_res<2>() == cudaSuccess) slots = resident_slots<2>(C, smem); break;
+    case 4: if (configure_res<4>() == cudaSuccess) slots = resident_slots<4>(C, smem); break;
+    case 8: if (configure_res<8>() == cudaSuccess) slots = resident_slots<8>(C, smem); break;
+    case 16: if (configure_res<16>() == cudaSuccess) slots = resident_slots<16>(C, smem); break;
+    case 32: if (configure_res<32>() == cudaSuccess) slots = resident_slots<32>(C, smem); break;
+  }
+  return make_plan(batch, n_steps, slots);
+}
+
+cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s, int* launches,
+                                 const ResHooks* hooks) {
   FineArgs a = args;
   fine_args_floats(a);
   switch (a.nv / VPT) {
-    case 2: return launch_res<2>(a, C, smem, s, launches);
-    case 4: return launch_res<4>(a, C, smem, s, launches);
-    case 8: return launch_res<8>(a, C, smem, s, launches);
-    case 16: return launch_res<16>(a, C, smem, s, launches);
-    case 32: return launch_res<32>(a, C, smem, s, launches);
+    case 2: return launch_res<2>(a, C, smem, s, launches, hooks);
+    case 4: return launch_res<4>(a, C, smem, s, launches, hooks);
+    case 8: return launch_res<8>(a, C, smem, s, launches, hooks);
+    case 16: return launch_res<16>(a, C, smem, s, launches, hooks);
+    case 32: return launch_res<32>(a, C, smem, s, launches, hooks);
   }
   return cudaErrorInvalidValue;
 }

@@ -128,9 +128,27 @@ cudaError_t launch_fine(const FineArgs& a, int vpt, bool fp32, size_t smem,
 // cluster size (0: shape not supported) and the dynamic shared memory.
 int fine_resident_cluster(int nx, int nv, bool fp32, bool adapt, int flux_rule, size_t* smem);
 size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, int C);
-// *launches (nullable) receives the kernel launches made: a batch larger
-// than the GPU holds at once runs in rounds.
-cudaError_t launch_fine_resident(const FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches = nullptr);
+// Launch plan of the resident kernel for one call: a batch larger than the
+// GPU holds at once runs as batch x chunks items of L steps in rounds
+// (launches0 launches), then the r steps left over (launches1 launches).
+struct ResPlan {
+  int batch, chunks;
+  int64_t L, r;
+  int per_round0, per_round1, launches0, launches1;
+  int launches() const { return launches0 + launches1; }
+  int final_launch(int state) const;  // the launch after which the state is final
+};
+ResPlan resident_plan(int nv, int batch, int64_t n_steps, int C, size_t smem);
+// Events around the launches of one call (null entries are skipped): the
+// stream waits for before[i] ahead of launch i and records after[i] behind it.
+struct ResHooks {
+  static constexpr int kMax = 64;
+  cudaEvent_t before[kMax];
+  cudaEvent_t after[kMax];
+};
+// *launches (nullable) receives the kernel launches made.
+cudaError_t launch_fine_resident(const FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches = nullptr,
+                                 const ResHooks* hooks = nullptr);
 
 // Arguments of the macroscopic kernels (coarse step, lift, correction).
 struct MacroArgs {

@@ -190,3 +190,26 @@ def test_batch_rejects_full_state():
                         np.ascontiguousarray(w.g0.astype(np.float32)), mode=mm.MM_PARAREAL_FULL_STATE)
     assert e.value.status == mm.MM_ERR_INVALID
     b.close()
+
+
+def test_parareal_overlapped_with_fine_rounds():
+    """More slice states than the GPU holds at once (320 states of Nx=256,
+    Nv=32, one CTA each, two per SM), 400 fine steps per slice: the resident
+    kernel runs in rounds of step chunks, the rest of the coarse guess and
+    its lifting run on a second stream during the first round, and the
+    correction of the slices whose last chunk has run during the last
+    round.  Two iterations against the oracle's Algorithm 1."""
+    N = 320
+    w = W.batched(256, 32, 1e-2, n_slices=N)
+    p = params(256, 32, 1e-2, mm.MM_FP32G, v_max=w.v_max, rho_bar=1.0, fine_kernel=2)
+    ctx = mm.mm_create(p)
+    w.t_end = N * 400 * mm.mm_query(ctx, 1.0)["dt_limit"] * (1 - 1e-9)
+    ctx.close()
+    p, out, info = _parareal(mm.MM_FP32G, w, 2, fine_kernel=2)
+    assert info["fine_launches"] > 2, info  # rounds in both iterations
+    ref, err, it = O.parareal(oparams(p), w.rho0, w.g0, w.t_end, N, 2)
+    assert info["iterations"] == it == 2
+    assert rel(out, ref) <= FP32_TOL, rel(out, ref)
+    # successive errors: the FP32 path's density carries ~1e-7 rounding
+    assert np.allclose(info["err"], err, rtol=1e-3, atol=1e-6), (info["err"], err)
+    assert info["mass_drift"] <= 1e-12
