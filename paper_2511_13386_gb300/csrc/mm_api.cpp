@@ -838,7 +838,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   // sequential order: every dependency is an event.
   const FineChoice fc = fine_choice(c);
   const bool can_overlap = !full && fc.kernel == 2 && wsb == 0;
-  auto plan_for = [&](int batch) { return mmk::resident_plan(nv, batch, nf, fc.C, fc.res_smem); };
+  auto plan_for = [&](int batch) { return mmk::resident_plan(nx, nv, batch, nf, fc.C, fc.res_smem); };
   if (can_overlap && !c->side) {
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) c->side = nullptr;
     for (cudaEvent_t& ev : c->ov)

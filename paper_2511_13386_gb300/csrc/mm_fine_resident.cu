@@ -129,7 +129,10 @@ __device__ double block_scan_d(double v, double* red, double* tot) {
   return off + v;
 }
 
-template <int LG>
+// RC: the run length R of a lane group when it is known at compile time
+// (the sweep loop then unrolls completely, without runtime branches), 0
+// when it is taken from the shape at run time.
+template <int LG, int RC>
 __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, int C) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int HALF = LG / 2;
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   const int rl = (r + C - 1) % C, rr = (r + 1) % C;
   const int nwc = n >> 5;                // warps that own cells
   const bool has_cell = tid < n;
-  const int R = n / NGRP;                // columns per group
+  const int R = RC ? RC : n / NGRP;      // columns per group
   const bool warp_local = R == LG;       // thread t's cell t lies in its own group's run
 
   const ResMap Mp = res_map(n, nv, LG, C);
@@ -468,6 +471,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
       // end of the run) into the slot of column i - 1
       if (k + 3 <= R) ldcol(P, k + 3 < R ? col(i + 3) : rnext);
     };
+#pragma unroll
     for (int k = 0; k < R; k += 4) {
       body(k + 0, R0, R1, R2);
       body(k + 1, R1, R2, R3);
@@ -565,7 +569,7 @@ size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, 
 
 // Clusters of the resident kernel that the GPU holds at once for this
 // launch shape (the occupancy calculator's answer, cached per shape).
-template <int LG>
+template <int LG, int RC>
 static int resident_slots(int C, size_t smem) {
   static std::mutex mu;
   static int dev_c[4] = {-1, -1, -1, -1}, slots_c[4] = {0, 0, 0, 0};
@@ -578,7 +582,7 @@ static int resident_slots(int C, size_t smem) {
   int slots = 0;
   if (C == 1) {
     int per_sm = 0, n_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fine_resident_kernel<LG>, T, smem) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fine_resident_kernel<LG, RC>, T, smem) == cudaSuccess &&
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       slots = per_sm * n_sm;
   } else {
@@ -593,7 +597,7 @@ static int resident_slots(int C, size_t smem) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&slots, fine_resident_kernel<LG>, &cfg) != cudaSuccess) slots = 0;
+    if (cudaOccupancyMaxActiveClusters(&slots, fine_resident_kernel<LG, RC>, &cfg) != cudaSuccess) slots = 0;
   }
   cudaGetLastError();  // a failed query leaves no sticky error; chunking is then off
   dev_c[ci] = dev;
@@ -636,11 +640,11 @@ static int resident_chunks(int batch, int64_t n_steps, int slots) {
   return best;
 }
 
-template <int LG>
+template <int LG, int RC>
 static cudaError_t configure_res() {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG>,
+    cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG, RC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -671,12 +675,12 @@ int ResPlan::final_launch(int state) const {
   return (int)(((int64_t)(chunks - 1) * batch + state) / per_round0);
 }
 
-template <int LG>
+template <int LG, int RC>
 static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches,
                               const ResHooks* hooks) {
-  cudaError_t e0 = configure_res<LG>();
+  cudaError_t e0 = configure_res<LG, RC>();
   if (e0 != cudaSuccess) return e0;
-  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG>(C, smem));
+  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG, RC>(C, smem));
   const int64_t L = q.L, r = q.r;
   if (launches) *launches = 0;
   int li = 0;  // launch index
@@ -705,7 +709,7 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = C > 1 ? 1 : 0;  // C == 1: a plain launch
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG>, (const FineArgs)a, C);
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG, RC>, (const FineArgs)a, C);
       if (e != cudaSuccess) return e;
       if (launches) ++*launches;
       if (hooks && li < ResHooks::kMax && hooks->after[li]) {
@@ -717,16 +721,37 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
   return cudaSuccess;
 }
 
-ResPlan resident_plan(int nv, int batch, int64_t n_steps, int C, size_t smem) {
+// The run length of a lane group for a shape: the CTA's cells n = nx / C
+// over T / LG groups.  The common run of 8 columns has its own unrolled
+// instance.
+static int run_length(int nx, int nv, int C) { return (nx / C) / (T / (nv / VPT)); }
+
+template <int LG>
+static int plan_slots(int nx, int C, size_t smem) {
+  if (run_length(nx, LG * VPT, C) == 8) {
+    if (configure_res<LG, 8>() != cudaSuccess) return 0;
+    return resident_slots<LG, 8>(C, smem);
+  }
+  if (configure_res<LG, 0>() != cudaSuccess) return 0;
+  return resident_slots<LG, 0>(C, smem);
+}
+
+ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem) {
   int slots = 0;
   switch (nv / VPT) {
-    case 2: if (configure_res<2>() == cudaSuccess) slots = resident_slots<2>(C, smem); break;
-    case 4: if (configure_res<4>() == cudaSuccess) slots = resident_slots<4>(C, smem); break;
-    case 8: if (configure_res<8>() == cudaSuccess) slots = resident_slots<8>(C, smem); break;
-    case 16: if (configure_res<16>() == cudaSuccess) slots = resident_slots<16>(C, smem); break;
-    case 32: if (configure_res<32>() == cudaSuccess) slots = resident_slots<32>(C, smem); break;
+    case 2: slots = plan_slots<2>(nx, C, smem); break;
+    case 4: slots = plan_slots<4>(nx, C, smem); break;
+    case 8: slots = plan_slots<8>(nx, C, smem); break;
+    case 16: slots = plan_slots<16>(nx, C, smem); break;
+    case 32: slots = plan_slots<32>(nx, C, smem); break;
   }
   return make_plan(batch, n_steps, slots);
+}
+
+template <int LG>
+static cudaError_t launch_lg(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches, const ResHooks* hooks) {
+  if (run_length(a.nx, a.nv, C) == 8) return launch_res<LG, 8>(a, C, smem, s, launches, hooks);
+  return launch_res<LG, 0>(a, C, smem, s, launches, hooks);
 }
 
 cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s, int* launches,
@@ -734,11 +759,11 @@ cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaS
   FineArgs a = args;
   fine_args_floats(a);
   switch (a.nv / VPT) {
-    case 2: return launch_res<2>(a, C, smem, s, launches, hooks);
-    case 4: return launch_res<4>(a, C, smem, s, launches, hooks);
-    case 8: return launch_res<8>(a, C, smem, s, launches, hooks);
-    case 16: return launch_res<16>(a, C, smem, s, launches, hooks);
-    case 32: return launch_res<32>(a, C, smem, s, launches, hooks);
+    case 2: return launch_lg<2>(a, C, smem, s, launches, hooks);
+    case 4: return launch_lg<4>(a, C, smem, s, launches, hooks);
+    case 8: return launch_lg<8>(a, C, smem, s, launches, hooks);
+    case 16: return launch_lg<16>(a, C, smem, s, launches, hooks);
+    case 32: return launch_lg<32>(a, C, smem, s, launches, hooks);
   }
   return cudaErrorInvalidValue;
 }

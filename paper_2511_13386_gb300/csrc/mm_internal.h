@@ -138,7 +138,7 @@ struct ResPlan {
   int launches() const { return launches0 + launches1; }
   int final_launch(int state) const;  // the launch after which the state is final
 };
-ResPlan resident_plan(int nv, int batch, int64_t n_steps, int C, size_t smem);
+ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem);
 // Events around the launches of one call (null entries are skipped): the
 // stream waits for before[i] ahead of launch i and records after[i] behind it.
 struct ResHooks {
