@@ -131,9 +131,11 @@ __device__ double block_scan_d(double v, double* red, double* tot) {
 
 // RC: the run length R of a lane group when it is known at compile time
 // (the sweep loop then unrolls completely, without runtime branches), 0
-// when it is taken from the shape at run time.
-template <int LG, int RC>
-__global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, int C) {
+// when it is taken from the shape at run time; CC likewise for the cluster
+// size (the loops over the cluster's CTAs unroll).
+template <int LG, int RC, int CC>
+__global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, int C_arg) {
+  const int C = CC ? CC : C_arg;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int HALF = LG / 2;
   constexpr int NGRP = T / LG;
@@ -569,7 +571,7 @@ size_t fine_resident_smem(int nx, int nv, bool fp32, bool adapt, int flux_rule, 
 
 // Clusters of the resident kernel that the GPU holds at once for this
 // launch shape (the occupancy calculator's answer, cached per shape).
-template <int LG, int RC>
+template <int LG, int RC, int CC>
 static int resident_slots(int C, size_t smem) {
   static std::mutex mu;
   static int dev_c[4] = {-1, -1, -1, -1}, slots_c[4] = {0, 0, 0, 0};
@@ -582,7 +584,7 @@ static int resident_slots(int C, size_t smem) {
   int slots = 0;
   if (C == 1) {
     int per_sm = 0, n_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fine_resident_kernel<LG, RC>, T, smem) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fine_resident_kernel<LG, RC, CC>, T, smem) == cudaSuccess &&
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       slots = per_sm * n_sm;
   } else {
@@ -597,7 +599,7 @@ static int resident_slots(int C, size_t smem) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&slots, fine_resident_kernel<LG, RC>, &cfg) != cudaSuccess) slots = 0;
+    if (cudaOccupancyMaxActiveClusters(&slots, fine_resident_kernel<LG, RC, CC>, &cfg) != cudaSuccess) slots = 0;
   }
   cudaGetLastError();  // a failed query leaves no sticky error; chunking is then off
   dev_c[ci] = dev;
@@ -640,11 +642,11 @@ static int resident_chunks(int batch, int64_t n_steps, int slots) {
   return best;
 }
 
-template <int LG, int RC>
+template <int LG, int RC, int CC>
 static cudaError_t configure_res() {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG, RC>,
+    cudaError_t e = cudaFuncSetAttribute(fine_resident_kernel<LG, RC, CC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -675,12 +677,12 @@ int ResPlan::final_launch(int state) const {
   return (int)(((int64_t)(chunks - 1) * batch + state) / per_round0);
 }
 
-template <int LG, int RC>
+template <int LG, int RC, int CC>
 static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches,
                               const ResHooks* hooks) {
-  cudaError_t e0 = configure_res<LG, RC>();
+  cudaError_t e0 = configure_res<LG, RC, CC>();
   if (e0 != cudaSuccess) return e0;
-  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG, RC>(C, smem));
+  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG, RC, CC>(C, smem));
   const int64_t L = q.L, r = q.r;
   if (launches) *launches = 0;
   int li = 0;  // launch index
@@ -709,7 +711,7 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = C > 1 ? 1 : 0;  // C == 1: a plain launch
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG, RC>, (const FineArgs)a, C);
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, fine_resident_kernel<LG, RC, CC>, (const FineArgs)a, C);
       if (e != cudaSuccess) return e;
       if (launches) ++*launches;
       if (hooks && li < ResHooks::kMax && hooks->after[li]) {
@@ -723,17 +725,19 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
 
 // The run length of a lane group for a shape: the CTA's cells n = nx / C
 // over T / LG groups.  The common run of 8 columns has its own unrolled
-// instance.
+// instances (with the cluster of 4 fixed too, the batched workload's).
 static int run_length(int nx, int nv, int C) { return (nx / C) / (T / (nv / VPT)); }
+
+template <int LG, int RC, int CC>
+static int slots_of(int C, size_t smem) {
+  if (configure_res<LG, RC, CC>() != cudaSuccess) return 0;
+  return resident_slots<LG, RC, CC>(C, smem);
+}
 
 template <int LG>
 static int plan_slots(int nx, int C, size_t smem) {
-  if (run_length(nx, LG * VPT, C) == 8) {
-    if (configure_res<LG, 8>() != cudaSuccess) return 0;
-    return resident_slots<LG, 8>(C, smem);
-  }
-  if (configure_res<LG, 0>() != cudaSuccess) return 0;
-  return resident_slots<LG, 0>(C, smem);
+  if (run_length(nx, LG * VPT, C) == 8) return C == 4 ? slots_of<LG, 8, 4>(C, smem) : slots_of<LG, 8, 0>(C, smem);
+  return slots_of<LG, 0, 0>(C, smem);
 }
 
 ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem) {
@@ -750,8 +754,11 @@ ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t 
 
 template <int LG>
 static cudaError_t launch_lg(FineArgs& a, int C, size_t smem, cudaStream_t s, int* launches, const ResHooks* hooks) {
-  if (run_length(a.nx, a.nv, C) == 8) return launch_res<LG, 8>(a, C, smem, s, launches, hooks);
-  return launch_res<LG, 0>(a, C, smem, s, launches, hooks);
+  if (run_length(a.nx, a.nv, C) == 8) {
+    if (C == 4) return launch_res<LG, 8, 4>(a, C, smem, s, launches, hooks);
+    return launch_res<LG, 8, 0>(a, C, smem, s, launches, hooks);
+  }
+  return launch_res<LG, 0, 0>(a, C, smem, s, launches, hooks);
 }
 
 cudaError_t launch_fine_resident(const FineArgs& args, int C, size_t smem, cudaStream_t s, int* launches,
