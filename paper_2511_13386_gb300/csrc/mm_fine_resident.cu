@@ -141,8 +141,11 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   constexpr int NGRP = T / LG;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int nx = A.nx, nv = A.nv;
-  const int n = nx / C;                  // cells (and interfaces) of this CTA
+  // shape: nv = 8 LG always; with the run length fixed, the CTA's cells
+  // n = R x (groups) too, and with the cluster size also nx = n C
+  const int nv = LG * VPT;
+  const int n = RC ? RC * NGRP : A.nx / C;  // cells (and interfaces) of this CTA
+  const int nx = (RC && CC) ? n * CC : A.nx;
   const int r = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
   // work item of this cluster: a chunk of A.n_steps steps of one state
   // (items are numbered chunk-major, item = chunk x batch + state, so a
