@@ -403,7 +403,14 @@ __device__ void lift_block(const FineArgs& A, const double* rho, double rb, G* g
 // density first.  buf0/buf1 are the two step buffers (the last step writes
 // buf0); the column arrays are carved from colsmem (shared memory, up to
 // `budget` bytes) and colglob (global memory, the fields that do not fit).
-template <class G, int VPT, bool ADAPT>
+// Lanes of the sweep's layout for nv velocity nodes (see the host's layout
+// rule): two halves of nhp lanes, nhp the power of two >= nv / 2 / VPT.
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+
+// NXC, NVC: the state's nx and nv when fixed at compile time (0: taken from
+// the arguments); with them the per-cell loops of the macro phase unroll
+// (nx a multiple of the block) and the sweep's layout is constant.
+template <class G, int VPT, bool ADAPT, int NXC = 0, int NVC = 0>
 __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin, const G* gin, G* buf0, G* buf1,
                                            double* rout, uint8_t* mout, unsigned char* smem,
                                            unsigned char* colsmem, unsigned char* colglob, size_t budget) {
@@ -411,7 +418,20 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   using R = typename M::R;
 
   const int tid = threadIdx.x;
-  const int nx = A.nx, nv = A.nv, Lg = A.lanes;
+  constexpr int NHC = NVC ? NVC / 2 / VPT : 0;
+  constexpr int NHPC = NHC ? pow2_at_least(NHC) : 0;
+  const int nx = NXC ? NXC : A.nx, nv = NVC ? NVC : A.nv;
+  const int nh = NHC ? NHC : A.nh, nhp = NHPC ? NHPC : A.nhp, Lg = NHPC ? 2 * NHPC : A.lanes;
+  // every cell c of the state, interleaved over the block (cell c by thread
+  // c mod T); unrolled when the number of rows is a constant
+  auto cells = [&](auto&& f) {
+    if constexpr (NXC != 0 && NXC % kFineThreads == 0) {
+#pragma unroll
+      for (int k = 0; k < NXC / kFineThreads; ++k) f(k * kFineThreads + (int)threadIdx.x);
+    } else {
+      for (int c = threadIdx.x; c < nx; c += kFineThreads) f(c);
+    }
+  };
   constexpr int T = kFineThreads;
 
   double* red = reinterpret_cast<double*>(smem);
@@ -440,15 +460,15 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   const int lig = tid % Lg;                // lane in group
   const int grp = tid / Lg;
   const int ngrp = T / Lg;
-  const bool pos = lig >= A.nhp;
-  const int hl = pos ? lig - A.nhp : lig;  // lane within its half
-  const bool active = hl < A.nh;
+  const bool pos = lig >= nhp;
+  const int hl = pos ? lig - nhp : lig;  // lane within its half
+  const bool active = hl < nh;
   const int j0 = pos ? nv / 2 + hl * VPT : hl * VPT;
   const bool first_lane = active && j0 == 0;
   const bool last_lane = active && j0 + VPT == nv;
   const int warp_base = (tid & 31) - lig;  // first lane of this group in the warp
-  const int src_left = warp_base + ((lig == A.nhp) ? A.nh - 1 : max(lig - 1, 0));
-  const int src_right = warp_base + ((lig == A.nh - 1) ? A.nhp : min(lig + 1, Lg - 1));
+  const int src_left = warp_base + ((lig == nhp) ? nh - 1 : max(lig - 1, 0));
+  const int src_right = warp_base + ((lig == nh - 1) ? nhp : min(lig + 1, Lg - 1));
   // which of the four end values (g_0, g_1, g_{nv-2}, g_{nv-1}) this lane stores
   int end_slot = -1;
   if (VPT == 1 && active) end_slot = j0 == 0 ? 0 : j0 == 1 ? 1 : j0 == nv - 2 ? 2 : j0 == nv - 1 ? 3 : -1;
@@ -489,11 +509,11 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   double rb = A.rho_bar;
   {
     double s = 0.0;
-    for (int c = tid; c < nx; c += T) {
+    cells([&](int c) {
       const double r = rin[c];
       C.rho[c] = M::c(r);
       s += r;
-    }
+    });
     if (isnan(rb)) rb = block_sum_d(s, red) / nx;
   }
   const R Rrb = M::c(rb);
@@ -507,7 +527,8 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   // store.
   auto reduce_store = [&](int i, bool valid, G p, G q) {
     G pe = G(0);
-    for (int m = A.nhp >> 1; m >= 1; m >>= 1) {
+#pragma unroll
+    for (int m = nhp >> 1; m >= 1; m >>= 1) {
       const G op = __shfl_xor_sync(0xffffffffu, p, m);
       if constexpr (sizeof(G) == 4) {
         const G oe = __shfl_xor_sync(0xffffffffu, pe, m);
@@ -519,7 +540,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       }
       if constexpr (ADAPT) q += __shfl_xor_sync(0xffffffffu, q, m);
     }
-    const int src = warp_base + A.nhp;
+    const int src = warp_base + nhp;
     const G pp = __shfl_sync(0xffffffffu, p, src);
     G ppe = G(0), qq = G(0);
     if constexpr (sizeof(G) == 4) ppe = __shfl_sync(0xffffffffu, pe, src);
@@ -565,7 +586,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     }
   }
   if constexpr (ADAPT) {
-    for (int c = tid; c < nx; c += T) { C.kin1[c] = 1; C.kin2[c] = 1; }
+    cells([&](int c) { C.kin1[c] = 1; C.kin2[c] = 1; });
   }
   __syncthreads();
 
@@ -635,7 +656,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       C.base[tid] = M::add(rr[64 + w], ex_lane);   // prefix before this thread's chunk
       const R meanS = rr[96];
       __syncthreads();
-      for (int c = tid; c < nx; c += T) {  // E^n into slot 0 of the sweep constants (+ low part)
+      cells([&](int c) {  // E^n into slot 0 of the sweep constants (+ low part)
         const R E = M::sub(M::add(C.base[c >> lcpt], C.S[c]), meanS);
         if constexpr (sizeof(G) == 4) {
           C.par[4 * c] = E.hi;
@@ -645,7 +666,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           C.par[4 * c + 1] = 0.0;
           if constexpr (ADAPT) C.par[4 * c + 2] = C.rho[c];  // density copy for the criteria
         }
-      }
+      });
       __syncthreads();  // rho final for this step; E of all cells visible
     }
 
@@ -670,7 +691,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         const ff k1 = {A.f_k1, A.f_k1_lo};
         auto rho_f = [&](int c) { return C.rho[wrapi(c, nx)]; };
         ff jsum = {0.f, 0.f};
-        for (int c = tid; c < nx; c += T) {
+        cells([&](int c) {
           const ff e1 = ff_sub_abs(rho_f(c + 1), rho_f(c - 1));
           const ff e2 = ff_sub_abs(rho_f(c + 2), rho_f(c - 2));
           const ff e3 = ff_sub_abs(rho_f(c + 3), rho_f(c - 3));
@@ -682,10 +703,10 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           C.par[4 * c + 2] = D1.hi;  // d rho / dx for the second pass
           Jf[c] = J;
           jsum = ff_add_abs(jsum, J);
-        }
+        });
         const float meanJ = block_sum_ff(jsum, red).hi * A.f_inv_nx;  // (syncs: Jc visible)
         const float rbf = rb_f;
-        for (int c = tid; c < nx; c += T) {
+        cells([&](int c) {
           const ff J0 = Jf[c];
           const ff Jm1 = Jf[wrapi(c - 1, nx)], Jp1 = Jf[wrapi(c + 1, nx)];
           const ff Jm2 = Jf[wrapi(c - 2, nx)], Jp2 = Jf[wrapi(c + 2, nx)];
@@ -712,23 +733,23 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           if (!cur) s = big_R ? 1 : 0;
           else s = (!gl && !gr && !big_R) ? 0 : 1;
           cell_nxt[c] = s;
-        }
+        });
       } else {
         const double inv_dx = A.inv_dx;
         auto rho_d = [&](int c) { return C.par[4 * wrapi(c, nx) + 2]; };
         auto E_d = [&](int c) { return C.par[4 * wrapi(c, nx)]; };
         double jsum = 0.0;
-        for (int c = tid; c < nx; c += T) {
+        cells([&](int c) {
           double d1 = 0.0;
           for (int k = -3; k <= 3; ++k) d1 += kFD[0][k + 3] * rho_d(c + k);
           d1 *= inv_dx;
           const double Ec = 0.5 * (E_d(c - 1) + E_d(c));
           C.jd[c] = d1 - Ec * rho_d(c);
           jsum += C.jd[c];
-        }
+        });
         const double meanJ = block_sum_d(jsum, red) / nx;  // (syncs: Jc visible)
         const double r2 = 1.0 / (A.dx * A.dx), r3 = r2 / A.dx;
-        for (int c = tid; c < nx; c += T) {
+        cells([&](int c) {
           double d1r = 0.0, d1J = 0.0, d2J = 0.0, d3J = 0.0;
           for (int k = -3; k <= 3; ++k) {
             const double jk = C.jd[wrapi(c + k, nx)];
@@ -753,7 +774,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           if (!cur) s = big_R ? 1 : 0;
           else s = (nl <= A.thr_g && nr <= A.thr_g && !big_R) ? 0 : 1;
           cell_nxt[c] = s;
-        }
+        });
       }
       __syncthreads();  // cell_cur of all cells visible
 
@@ -816,7 +837,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     }
 
     // J and the sweep constants: E+/dv, E-/dv, P = <X>, J
-    for (int c = tid; c < nx; c += T) {
+    cells([&](int c) {
       const int cl = wrapi(c - 1, nx), cr = wrapi(c + 1, nx);
       G* pr = C.par + 4 * c;
       const G e = pr[0];
@@ -842,7 +863,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       } else {
         pr[3] = M::flux_J(C.rho[c], C.rho[cr], e, g_inv_dx);
       }
-    }
+    });
     __syncthreads();
     if constexpr (ADAPT) {
       if (tid == 0) kin_total += rint[1];
@@ -876,22 +897,22 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   auto macro_C_ampere = [&]() {
     if constexpr (F32) {
       ff fsum = {0.f, 0.f};
-      for (int c = tid; c < nx; c += T) {
+      cells([&](int c) {
         const ff F = is_kin(c) ? flux_kin(c) : flux_fluid(c);
         C.fk[c] = F.hi;
         C.par[4 * c + 1] = F.lo;
         fsum = ff_add_abs(fsum, F);
-      }
+      });
       const ff Fbar = ff_mul(block_sum_ff(fsum, red), Rinv_nx);  // (syncs: fluxes visible)
       const ff mdx = {-Rdx.hi, -Rdx.lo};
-      for (int c = tid; c < nx; c += T) {
+      cells([&](int c) {
         const int cl = wrapi(c - 1, nx);
         const ff Fl = {C.fk[cl], C.par[4 * cl + 1]}, Fc = {C.fk[c], C.par[4 * c + 1]};
         C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fc);
         const ff E = ff_add(ff{C.par[4 * c], C.elo[c]}, ff_mul(ff_sub(Fc, Fbar), mdx));
         C.par[4 * c] = E.hi;
         C.elo[c] = E.lo;
-      }
+      });
     }
   };
   auto macro_C = [&]() {
@@ -900,14 +921,14 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     } else if (A.flux_rule == 0) {
       // each interface flux is evaluated by both of its cells, from the same
       // inputs, so the two evaluations are bitwise equal and mass telescopes
-      for (int c = tid; c < nx; c += T) {
+      cells([&](int c) {
         const int cl = wrapi(c - 1, nx);
         const R Fl = is_kin(cl) ? flux_kin(cl) : flux_fluid(cl);
         const R Fc = is_kin(c) ? flux_kin(c) : flux_fluid(c);
         C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fc);
-      }
+      });
     } else {
-      for (int c = tid; c < nx; c += T) {
+      cells([&](int c) {
         const int cl = wrapi(c - 1, nx);
         R Fr, Fl;
         if (!ADAPT || cell_cur[c]) {
@@ -918,7 +939,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           Fl = flux_fluid(cl);
         }
         C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fr);
-      }
+      });
     }
   };
 
@@ -1025,25 +1046,25 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
 
   // ---- epilogue
   int bad = 0;
-  for (int c = tid; c < nx; c += T) {
+  cells([&](int c) {
     const double r = M::tod(C.rho[c]);
     rout[c] = r;
     if (!isfinite(r)) bad = 1;
     if (mout) mout[c] = ADAPT ? cell_cur[c] : 1;
-  }
+  });
   if (bad) atomicExch(A.status, (int)MM_ERR_UNSTABLE);
   if (tid == 0 && A.kin_count) atomicAdd(A.kin_count, (unsigned long long)kin_total * (unsigned long long)nv);
 }
 
-// One CTA per state of a uniform batch.
-template <class G, int VPT, bool ADAPT>
+// One CTA per state of a uniform batch (NXC, NVC: see fine_state).
+template <class G, int VPT, bool ADAPT, int NXC = 0, int NVC = 0>
 __global__ void __launch_bounds__(kFineThreads, 1) fine_kernel(const FineArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t st = blockIdx.x;
   const size_t sz = (size_t)A.nx * A.nv;
   unsigned char* colglob =
       A.col_ws ? reinterpret_cast<unsigned char*>(A.col_ws) + st * A.col_ws_stride : nullptr;
-  fine_state<G, VPT, ADAPT>(A, A.rho_in + st * A.nx, reinterpret_cast<const G*>(A.g_in) + st * sz,
+  fine_state<G, VPT, ADAPT, NXC, NVC>(A, A.rho_in + st * A.nx, reinterpret_cast<const G*>(A.g_in) + st * sz,
                             reinterpret_cast<G*>(A.g_buf0) + st * sz, reinterpret_cast<G*>(A.g_buf1) + st * sz,
                             A.rho_out + st * A.nx, A.mask_out ? A.mask_out + st * A.nx : nullptr, smem,
                             smem + 8 * kRedSlots, colglob, kColBudgetFine);
@@ -1091,21 +1112,28 @@ __global__ void __launch_bounds__(kFineThreads, 1)
 
 // ---------------------------------------------------------------- launch --
 
-template <class G, int VPT, bool ADAPT>
+template <class G, int VPT, bool ADAPT, int NXC = 0, int NVC = 0>
 static cudaError_t launch_t(const FineArgs& a, size_t smem, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fine_kernel<G, VPT, ADAPT>,
+    cudaError_t e = cudaFuncSetAttribute(fine_kernel<G, VPT, ADAPT, NXC, NVC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fine_kernel<G, VPT, ADAPT><<<a.batch, kFineThreads, smem, s>>>(a);
+  fine_kernel<G, VPT, ADAPT, NXC, NVC><<<a.batch, kFineThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+// Instances with the shape fixed at compile time: FP32 g, 8 nodes per lane,
+// Nx = 4096 and Nv = 128 (the hybrid-adaptation grid); every other shape
+// takes the runtime-shape kernel.
 template <class G, int VPT>
 static cudaError_t launch_v(const FineArgs& a, size_t smem, cudaStream_t s) {
+  if constexpr (sizeof(G) == 4 && VPT == 8) {
+    if (a.nx == 4096 && a.nv == 128)
+      return a.adapt ? launch_t<G, VPT, true, 4096, 128>(a, smem, s) : launch_t<G, VPT, false, 4096, 128>(a, smem, s);
+  }
   return a.adapt ? launch_t<G, VPT, true>(a, smem, s) : launch_t<G, VPT, false>(a, smem, s);
 }
 
