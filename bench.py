@@ -363,7 +363,12 @@ def run_ours(a, rank, world, dist):
     achieved_flops = FLOPS_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e12
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alg_gbs = BYTES_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e9
-    kname = (f"fine_resident_kernel<{q['lanes']}> (cluster of {q['cluster']})" if q["fine_kernel"] == 2
+    # the resident kernel's instance: lane-group width, run length of a group
+    # (8: the compile-time instance, else 0) and cluster size (4: likewise)
+    res_run = (NX // max(q["cluster"], 1)) // (256 // max(q["lanes"], 1)) if q["fine_kernel"] == 2 else 0
+    res_rc = 8 if res_run == 8 else 0
+    res_cc = 4 if (res_rc and q["cluster"] == 4) else 0
+    kname = (f"fine_resident_kernel<{q['lanes']}, {res_rc}, {res_cc}> (cluster of {q['cluster']})" if q["fine_kernel"] == 2
              else f"fine_kernel<{'float' if prec == mm.MM_FP32G else 'double'},{q['vpt']}>")
     roofline = {"bound": "alu", "achieved": round(achieved_flops, 3), "peak": round(fp32_peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved_flops / fp32_peak, 4),
@@ -462,7 +467,8 @@ def run_hybrid(a):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     launch_ms = statistics.mean(kin_ms)
     achieved = BYTES_PER_UPDATE * (upd / a.steps) / (launch_ms / 1e3) / 1e9
-    kname = f"fine_kernel<float,{q['vpt']},adapt>"
+    fixed = q["vpt"] == 8 and H_NX == 4096 and H_NV == 128  # the compile-time-shape instance
+    kname = f"fine_kernel<float,{q['vpt']},adapt{',4096,128' if fixed else ''}>"
     autotune = {"chosen": kname, f"candidates_ms_{window}_steps": {
         f"streaming {c['vpt']} nodes/lane": round(c["ms"], 3) for c in tune["candidates"]}}
     line = {"metric": "cell-updates/s", "value": upd / (total_ms / 1e3), "unit": "cell-updates/s", "n_gpus": 1,
