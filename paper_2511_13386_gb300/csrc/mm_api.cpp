@@ -924,7 +924,6 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
                    (double*)frho + (size_t)(k + 1) * nx, g_out, nullptr, rb, stats ? &fs : nullptr, s,
                    use_hooks ? &hooks : nullptr);
     if (st != MM_OK) return st;
-    if (k == 0 && p_split && !use_hooks) CK(cudaStreamWaitEvent(s, c->ov[1], 0), "overlap join");
     if (stats) {
       kin_total += fs.kinetic_updates;
       fine_ms += fs.elapsed_ms;
