@@ -214,3 +214,27 @@ def test_hybrid_large_ragged_grids(prec, nx):
     ctx.close()
     ro, go, mo, st, q = _check(p, rho, g, 25 * dt * (1 - 1e-9))
     assert 0 < mo.sum() < mo.size
+
+
+@pytest.mark.parametrize("adapt", [0, 1], ids=["full-kinetic", "adaptive"])
+@pytest.mark.parametrize("kernel", [0, 1], ids=["auto", "streaming"])
+def test_fixed_shape_streaming_instance(adapt, kernel):
+    """Nx = 4096, Nv = 128 in FP32 runs the streaming kernel's instance with
+    the shape fixed at compile time (unrolled per-cell loops, constant lane
+    layout): with and without adaptation, against the oracle."""
+    nx, nv = 4096, 128
+    if adapt:
+        w = W.hybrid(nx, nv, 1e-3, v_max=10.0)
+        rho, g = w.with_batch(2)
+        p = params(nx, nv, 1e-3, mm.MM_FP32G, v_max=10.0, rho_bar=1.0, adapt=1, thr_g=w.thr_g, thr_R=w.thr_R,
+                   r_scale=w.r_scale, fine_kernel=kernel)
+    else:
+        w = W.batched(nx=nx, nv=nv, eps=0.05, v_max=10.0)
+        rho, g = w.with_batch(2)
+        p = params(nx, nv, 0.05, mm.MM_FP32G, v_max=10.0, rho_bar=1.0, fine_kernel=kernel)
+    ctx = mm.mm_create(p)
+    q = mm.mm_query(ctx, 1.0)
+    dt = q["dt_limit"]
+    assert q["fine_kernel"] == 1  # no resident shape holds 4096 x 128
+    ctx.close()
+    _check(p, rho, g, 20 * dt * (1 - 1e-9))
