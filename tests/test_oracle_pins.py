@@ -575,3 +575,64 @@ def test_bruteforce_rational_tiny_grid(adapt):
     assert np.abs(g_o - gg).max() <= 1e-14 * np.abs(gg).max()
     if adapt:
         assert 0 < sum(mm) < nx
+
+
+# ------------------------------------------- linear symbol of one step ---
+
+def _fine_symbol(p, dt, theta):
+    """The (Nv+1) x (Nv+1) matrix of one step of the scheme (every
+    interface kinetic, one flux per interface) on the Fourier mode e^{i theta
+    i} of a small perturbation of rho = rho_bar, g = 0, written out from the
+    step's definition: the Poisson prefix sum with its mean removed, the
+    flux J, the upwind x-fluxes of g, the projection P = <X> M, the
+    exponential relaxation g* = a g - b (X - P M + v M J) and the flux-form
+    density update with Phi = <v g*> / eps.  The field term E d_v g is
+    quadratic in the perturbation and drops out.  State (rho^, g^_0..)."""
+    v, w, M, _ = O.velocity_grid(p)
+    nv, dx, eps = p.nv, p.x_len / p.nx, p.eps
+    a = math.exp(-dt / eps ** 2)
+    b = eps * (1.0 - a)
+    z = np.exp(1j * theta)
+    vp, vm = np.maximum(v, 0.0), np.maximum(-v, 0.0)
+    sym_E = dx / (1.0 - 1.0 / z)                         # E^ per rho^
+    sym_J = (z - 1.0) / dx - p.rho_bar * sym_E           # J^ per rho^
+    sym_A = (vp * (1.0 - 1.0 / z) - vm * (z - 1.0)) / dx  # A^_j per g^_j
+    A = np.zeros((nv + 1, nv + 1), dtype=complex)
+    for col in range(nv + 1):
+        u = np.zeros(nv + 1, dtype=complex)
+        u[col] = 1.0
+        rho_h, g_h = u[0], u[1:]
+        X = sym_A * g_h
+        Pm = np.dot(w, X)
+        gs = a * g_h - b * (X - Pm * M + v * M * (sym_J * rho_h))
+        phi = np.dot(w, v * gs) / eps
+        A[0, col] = rho_h - (dt / dx) * (1.0 - 1.0 / z) * phi
+        A[1:, col] = gs
+    return A
+
+
+@pytest.mark.parametrize("eps", [1.0, 0.1, 0.01])
+def test_fine_matches_powers_of_its_linear_symbol(eps):
+    """A small cosine mode (amplitude 1e-7) in rho and in g, 12 steps of F:
+    the oracle equals A(theta)^12 applied to the mode to first order in the
+    amplitude.  A wrong upwind side, sign of the field, index of the
+    interface, projection weight or relaxation constant changes A."""
+    nx, nv, m, delta, n = 32, 16, 3, 1e-7, 12
+    p = P(nx=nx, nv=nv, eps=eps, rho_bar=1.0)
+    v, w, M, m2 = O.velocity_grid(p)
+    dt = O.dt_limit(p)
+    theta = 2 * np.pi * m / nx
+    i = np.arange(nx)
+    c = (v ** 2 - m2) * M                      # <c> = 0: a valid perturbation of g
+    rho0 = 1.0 + delta * np.cos(theta * i)
+    g0 = delta * np.outer(np.cos(theta * i), c)
+    rho, g, _, _ = O.fine(p, n, dt, rho0, g0)
+    u = np.concatenate(([delta], delta * c)).astype(complex)
+    un = np.linalg.matrix_power(_fine_symbol(p, dt, theta), n) @ u
+    zi = np.exp(1j * theta * i)
+    rho_pred = np.real(un[0] * zi)
+    g_pred = np.real(np.outer(zi, un[1:]))
+    assert np.abs((rho - 1.0) - rho_pred).max() <= 1e-5 * np.abs(rho_pred).max()
+    assert np.abs(g - g_pred).max() <= 1e-5 * np.abs(g_pred).max()
+    # and the perturbation did evolve: the prediction is not the identity
+    assert np.abs(rho_pred - delta * np.cos(theta * i)).max() > 1e-3 * delta
