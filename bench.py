@@ -69,6 +69,11 @@ def parse():
     return a
 
 
+# the default workload's name, the same on both arms of the benchmark
+BATCHED_WORKLOAD = ("batched parareal: Nx=1024, Nv=64 on [-8,8], eps=1e-2, T=1, N=128 slices, full kinetic, "
+                    "one parareal iteration per step")
+
+
 def kernel_only(a):
     """Launch one kernel of the hot path on the workload (for ncu captures):
     'fine' runs the fine propagator on all 128 slice states for --window
@@ -781,8 +786,7 @@ def main():
                 "unit": "cell-updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": 1e3 * statistics.mean(step_s), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "batched parareal, Nx=1024 Nv=64 eps=1e-2 N=128, full kinetic",
-                           "sample": sample},
+                "config": {"workload": BATCHED_WORKLOAD, "sample": sample},
                 "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
                                  "kind": "oracle", "sample": sample},
                 "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
@@ -816,8 +820,7 @@ def main():
             "ms_per_step": r["total_ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if a.precision == "fp32g" else "f64",
             "data": "synthetic",
-            "config": {"workload": "batched parareal: Nx=1024, Nv=64 on [-8,8], eps=1e-2, T=1, "
-                                   "N=128 slices, full kinetic, one parareal iteration per step",
+            "config": {"workload": BATCHED_WORKLOAD,
                        "precision": "FP32 g; float-float density, Poisson and moments"
                        if a.precision == "fp32g" else "FP64",
                        "fine_steps_per_slice": r["n_steps_fine"],
