@@ -337,7 +337,12 @@ typedef struct {
    slice's own g, and g^{n+1,k+1} = F_g(U^{n,k}) + (L G rho^{n,k+1} -
    L G rho^{n,k}) (the slices' g stay on the device, 2 (N+1) nx nv values).
    rho_slices_out [n_slices + 1][nx] double receives rho^{n,K}.  The call
-   synchronises the stream once per iteration (error test).
+   synchronises the stream once per iteration (error test).  In density mode,
+   when the resident fine kernel runs a batch in rounds of step chunks, part
+   of the coarse guess, the lifting and the correction runs on a second
+   stream that the context owns, ordered by events against the caller's
+   stream; the results are those of the sequential order, and the call
+   returns only after that work is complete.
    Errors: MM_ERR_INVALID, MM_ERR_UNSTABLE, MM_ERR_CUDA, MM_ERR_OOM. */
 MM_API mm_status parareal_run(mm_ctx* ctx, const mm_parareal_cfg* cfg,
                        const double* rho0, const void* g0,
