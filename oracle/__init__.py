@@ -7,9 +7,13 @@ Def. 1 and Algorithm 1, used to check the CUDA library.  Only ``tests/``,
 ``bench.py`` may import it.  It shares no code with the CUDA path; the two
 only meet through the seeded input generators.
 
-Parity unpinned (no printed value or closed form fixes them): the meaning of
-the adaptation thresholds (literal |R| vs eps^2 |R|), the discrete time
-derivative of E inside R, and lifting orders above one.
+Parity unpinned (no printed value or closed form fixes it): the discrete
+time derivative of E inside R.  Which scaling of the remainder criterion the
+paper means (literal |R| or eps^2 |R|) is a reading; both switches are pinned
+(exact-rational brute force and the threshold-crossing test), as is the
+cell-based density update of eq. S^HMM (brute force and its mass defect).
+Lifting orders above one are pinned to their continuous limit and to the
+scheme's relaxed perturbation, not to a printed value.
 """
 from __future__ import annotations
 

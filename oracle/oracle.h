@@ -20,11 +20,13 @@
  * Arrays: rho[nx], g[nx][nv] (v contiguous), E[nx], J[nx], mask[nx] (1 =
  * kinetic cell).  Every function is a pure function of its arguments.
  *
- * Parity unpinned (no closed form or printed value fixes them; any consistent
- * choice passes): the meaning of the adaptation thresholds (literal |R| vs
- * eps^2 |R|) and the discrete time derivative of E inside R.  The lifting
- * of orders two and three is pinned to its continuous limit and to the
- * scheme's own relaxed perturbation, not to a printed value.
+ * Parity unpinned (no closed form or printed value fixes it; any consistent
+ * choice passes): the discrete time derivative of E inside R.  Which
+ * scaling of the remainder criterion the paper means (literal |R| or
+ * eps^2 |R|) is a reading, but each switch is pinned, as is the cell-based
+ * density update (flux_rule = 1).  The lifting of orders two and three is
+ * pinned to its continuous limit and to the scheme's own relaxed
+ * perturbation, not to a printed value.
  */
 #ifndef ORACLE_H
 #define ORACLE_H

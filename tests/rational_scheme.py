@@ -62,10 +62,14 @@ def remainder(rho, E, rho_bar, dx, T):
 
 
 def step(c, rho, g, mask):
-    """One step of S^HMM with one flux per interface.
+    """One step of S^HMM.
 
     c: dict of exact constants: v, w, M (lists), m2, a, b, dx, dv, eps, dt,
-    rho_bar, adapt, thr_g, thr_R, r (all Fractions / ints).
+    rho_bar, adapt, thr_g, thr_R, r (all Fractions / ints), and optionally
+    flux_rule: 0 (default) one flux per interface, 1 the cell-based density
+    update as printed in eq. S^HMM (kinetic cell: the difference of the new
+    moments <xi g^{n+1}>/eps of its two interfaces, g^{n+1} being 0 on a
+    fluid interface; fluid cell: m2 times the difference of the two J).
     Returns (rho, g, mask) at t^{n+1}.
     """
     T = table1()
@@ -106,5 +110,17 @@ def step(c, rho, g, mask):
         gn[i] = [c["a"] * gc[j] - c["b"] * (X[j] - P * M[j] + v[j] * M[j] * J[i])
                  for j in range(nv)]
         Phi[i] = sum(w[j] * v[j] * gn[i][j] for j in range(nv)) / c["eps"]
+    if c.get("flux_rule", 0) == 1:
+        # eq. S^HMM as printed: rho_i += dt/dx * Jt_i with a per-cell flux
+        # difference chosen by the status of cell i at t^n.
+        mom = [sum(w[j] * v[j] * gn[i][j] for j in range(nv)) / c["eps"] for i in range(nx)]
+        rn = []
+        for i in range(nx):
+            if mask[i]:
+                Jt = -(mom[i] - mom[(i - 1) % nx])
+            else:
+                Jt = c["m2"] * (J[i] - J[(i - 1) % nx])
+            rn.append(rho[i] + c["dt"] / c["dx"] * Jt)
+        return rn, gn, new_mask
     rn = [rho[i] - c["dt"] / c["dx"] * (Phi[i] - Phi[(i - 1) % nx]) for i in range(nx)]
     return rn, gn, new_mask

@@ -547,25 +547,44 @@ def _exact_constants(p, dt):
                 r=Fr(p.eps * p.eps) if p.r_scale else Fr(1))
 
 
-@pytest.mark.parametrize("adapt", [False, True])
-def test_bruteforce_rational_tiny_grid(adapt):
-    """Nx=8, Nv=4, three steps in exact rationals: the oracle agrees to
-    1e-14 and the masks are identical."""
+# (adapt, flux_rule, r_scale, thr_R): the thresholds put eps^2 |R| and |R|
+# on different sides of thr_R for some cells (eps = 0.5, so the two scalings
+# differ by 4x and a plain eps would differ from both), and leave a mixed
+# kinetic/fluid mask, so the cell-based density update differs from the
+# one-flux rule.
+_BRUTE_CASES = [
+    (False, 0, 0, 100.0),
+    (True, 0, 0, 100.0),
+    (True, 1, 0, 500.0),
+    (True, 0, 1, 150.0),
+    (True, 1, 1, 150.0),
+]
+
+
+@pytest.mark.parametrize("adapt,flux_rule,r_scale,thr_R", _BRUTE_CASES)
+def test_bruteforce_rational_tiny_grid(adapt, flux_rule, r_scale, thr_R):
+    """Nx=8, Nv=4, three steps in exact rationals (eq. S^HMM with the status
+    rules of Sec. 2.3; the cell-based density update as printed when
+    flux_rule = 1; the remainder criterion scaled by eps^2 when r_scale = 1):
+    the oracle agrees to 1e-14 and the masks are identical."""
     nx, nv = 8, 4
     p = O.Params(nx=nx, nv=nv, eps=0.5, v_max=4.0, adapt=adapt, thr_g=2e-3,
-                 thr_R=100.0, rho_bar=1.0)
+                 thr_R=thr_R, rho_bar=1.0, r_scale=r_scale, flux_rule=flux_rule)
     rng = W.SplitMix64(99)
     rho = 1.0 + 0.2 * (rng.uniforms(nx) - 0.5)
     g = 0.01 * (rng.uniforms(nx * nv).reshape(nx, nv) - 0.5)
-    g[3:6] *= 1e-3
+    g[2:7] *= 1e-3      # cells 3..6: both interface norms below thr_g
     dt = 0.5 * O.dt_limit(p)
     c = _exact_constants(p, dt)
+    c["flux_rule"] = flux_rule
     mask = O.initial_status(p, rho, g)
     rr = [Fr(x) for x in rho]
     gg = [[Fr(x) for x in row] for row in g]
     mm = [int(x) for x in mask]
     r_o, g_o, m_o = rho.copy(), g.copy(), mask.copy()
+    saw_mixed = False
     for _ in range(3):
+        saw_mixed |= 0 < sum(mm) < nx
         rr, gg, mm = RS.step(c, rr, gg, mm)
         r_o, g_o, m_o, _ = O.fine_step(p, dt, r_o, g_o, m_o)
         assert m_o.tolist() == mm
@@ -574,7 +593,88 @@ def test_bruteforce_rational_tiny_grid(adapt):
     assert np.abs(r_o - rr).max() <= 1e-14
     assert np.abs(g_o - gg).max() <= 1e-14 * np.abs(gg).max()
     if adapt:
-        assert 0 < sum(mm) < nx
+        assert saw_mixed
+
+
+def test_bruteforce_cases_separate_the_two_remainder_scalings():
+    """The r_scale cases above are only a pin of the eps^2 factor if the
+    literal and the scaled criterion give different masks on their data."""
+    nx, nv = 8, 4
+    rng = W.SplitMix64(99)
+    rho = 1.0 + 0.2 * (rng.uniforms(nx) - 0.5)
+    g = 0.01 * (rng.uniforms(nx * nv).reshape(nx, nv) - 0.5)
+    g[2:7] *= 1e-3
+    masks = []
+    for r_scale in (0, 1):
+        p = O.Params(nx=nx, nv=nv, eps=0.5, v_max=4.0, adapt=True, thr_g=2e-3,
+                     thr_R=150.0, rho_bar=1.0, r_scale=r_scale)
+        m = O.initial_status(p, rho, g)
+        masks.append(O.update_status(p, rho, g, m).tolist())
+    assert masks[0] != masks[1]
+
+
+def test_cell_based_mass_defect_is_the_flux_mismatch_at_mixed_interfaces():
+    """Remark after Lemma 1: the cell-based update of eq. S^HMM is not
+    conservative.  Summing its per-cell flux differences, every interface
+    between two cells of the same status cancels, and an interface between a
+    kinetic cell i and a fluid cell i+1 leaves -(<xi g^{n+1}>/eps + m2 J);
+    the reverse order leaves the opposite.  So one step changes the mass
+    sum(rho) dx by exactly dt times the signed sum of that mismatch over the
+    mixed interfaces."""
+    w, p = _hybrid_small(1)
+    v, wq, M, m2 = O.velocity_grid(p)
+    dx = p.x_len / p.nx
+    x = (np.arange(w.nx) + 0.5) / w.nx
+    rho = 1.0 + 0.01 * np.cos(2 * np.pi * x)
+    g = w.g0.copy()
+    mask = O.initial_status(p, rho, g)
+    dt = O.dt_limit(p)
+    checked = 0
+    for _ in range(25):
+        E = O.poisson(p, rho)
+        J = O.flux_J(p, rho, E)
+        r1, g1, m1, _ = O.fine_step(p, dt, rho, g, mask)
+        mom = (g1 * (wq * v)[None, :]).sum(axis=1) / p.eps
+        left, right = mask.astype(int), np.roll(mask, -1).astype(int)
+        sign = right - left            # -1: kinetic|fluid, +1: fluid|kinetic
+        mismatch = sign * (mom + m2 * J)
+        want = dt * mismatch.sum()
+        got = (r1 - rho).sum() * dx
+        scale = dt * np.abs(mismatch).sum()
+        if 0 < mask.sum() < w.nx:
+            assert abs(got - want) <= 1e-12 * scale + 1e-16 * rho.sum() * dx
+            checked += abs(want) > 1e-6 * scale
+        else:
+            assert abs(got) <= 1e-15 * rho.sum() * dx
+        rho, g, mask = r1, g1, m1
+    assert checked > 0
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.03])
+def test_remainder_threshold_flips_exactly_at_eps2_scaled_R(eps):
+    """Sec. 2.3 compares |R_i| with thr_R; r_scale = 1 compares eps^2 |R_i|
+    (the O(eps^2) factor in front of R in eq. HigherOrderModel).  With g = 0
+    (both interface norms below thr_g) the status of a cell then depends on
+    the remainder alone, and it must flip exactly where thr_R crosses
+    eps^2 |R_i| (resp. |R_i|).  R_i is evaluated independently, in exact
+    rationals from the printed Table 1."""
+    nx, nv = 16, 8
+    x = (np.arange(nx) + 0.5) / nx
+    rho = 1.0 + 0.1 * np.cos(2 * np.pi * x) + 0.03 * np.sin(6 * np.pi * x)
+    dx = Fr(1, nx)
+    rr = [Fr(r) for r in rho]
+    R = [float(r) for r in RS.remainder(rr, RS.poisson(rr, Fr(1), dx), Fr(1), dx, RS.table1())]
+    g = np.zeros((nx, nv))
+    big = [i for i in range(nx) if abs(R[i]) > 1e-3 * max(map(abs, R))]
+    assert len(big) >= nx // 2
+    for r_scale, fac in ((1, eps * eps), (0, 1.0)):
+        for i in big:
+            for side, want in ((1 + 1e-6, 0), (1 - 1e-6, 1)):
+                p = O.Params(nx=nx, nv=nv, eps=eps, adapt=True, thr_g=1e-3,
+                             thr_R=fac * abs(R[i]) * side, rho_bar=1.0, r_scale=r_scale)
+                for start in (0, 1):    # fluid -> kinetic and kinetic -> fluid rules
+                    m = O.update_status(p, rho, g, np.full(nx, start, np.uint8))
+                    assert m[i] == want, (r_scale, i, side, start)
 
 
 # ------------------------------------------- linear symbol of one step ---
