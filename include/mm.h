@@ -130,8 +130,9 @@ typedef struct {
                           resident kernel whenever it applies. */
   int32_t fine_vpt;    /* velocity nodes per lane of the streaming kernel:
                           0 = the most that fits (8 in FP32, 4 in FP64, or
-                          fewer when nv requires); 1, 2, 4 or 8 (FP32) / 1,
-                          2, 4 (FP64) forces that lane layout
+                          fewer when nv requires; FP64 offers 8 only
+                          where 4 would need more than 32 lanes, nv =
+                          256); 1, 2, 4 or 8 forces that lane layout
                           (MM_ERR_INVALID if nv does not allow it).  The
                           batch engine always uses the default. */
 } mm_params;
@@ -208,30 +209,33 @@ MM_API mm_status mm_fine_propagate(mm_ctx* ctx, int32_t batch, double t_span,
                             mm_fine_stats* stats, void* stream);
 
 /* Size in bytes of the fixed device scratch array of
-   mm_fine_propagate_noalloc (64 MiB, held by every GPU that loads the
-   library until the process exits). */
+   mm_fine_propagate_noalloc (64 MiB).  The array is reserved on a device by
+   the first mm_create on that device and held until the process exits. */
 #define MM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
 /* mm_fine_propagate for callers that cannot allocate device memory when
    they run F.  The paper has no counterpart: this is a deployment variant of
-   the same kernel.  Such callers -- an application whose memory is all
+   the same propagator.  Such callers -- an application whose memory is all
    handed to its own pool, a real-time loop that must not reach the
    allocator or risk an out-of-memory failure mid-run -- create the context
-   once at start-up (mm_create allocates its small velocity tables there)
-   and then call this entry point, which allocates nothing: the scratch of
-   the fine kernel (second step buffer of g, status word, the column arrays
-   when they do not fit shared memory, and a copy of g_in when it aliases
-   g_out with an odd step count) lives in a static device array of
-   MM_NOALLOC_SCRATCH_BYTES inside the library.
-   Arguments and results are those of mm_fine_propagate, with three
-   differences: every array must be a 16-byte aligned device pointer (host
-   arrays would need staging buffers); stats->elapsed_ms is 0; the call's
-   scratch must fit the array.
-   The first call on a device looks up the array's device address on that
-   device (cudaGetSymbolAddress), so make that first call before any stream
-   capture.  Every call shares the one array and the array keeps the last
-   call's contents: calls that may run at the same time on the GPU (on
-   streams with no ordering between them) race on it and must not be issued.
+   once at start-up and then call this entry point, which allocates nothing:
+   the scratch of the fine kernel (the status word; for the streaming kernel
+   also its second step buffer of g, the column arrays when they do not fit
+   shared memory, and a copy of g_in when it aliases g_out with an odd step
+   count) lives in a static device array of MM_NOALLOC_SCRATCH_BYTES inside
+   the library.  mm_create does the set-up with the context's device
+   current: it looks up the array's device address (cudaGetSymbolAddress),
+   which reserves the array on that device, and loads the kernels of the
+   context's launch choice, so no call of this entry point loads anything.
+   The call runs the same kernel and launch shape as mm_fine_propagate would
+   for the context (the resident kernel where it applies, or the choice of
+   mm_autotune), so results are identical.  Arguments are those of
+   mm_fine_propagate, with three differences: every array must be a 16-byte
+   aligned device pointer (host arrays would need staging buffers);
+   stats->elapsed_ms is 0; the call's scratch must fit the array.  Every call
+   shares the one array and the array keeps the last call's contents: calls
+   that may run at the same time on the GPU (on streams with no ordering
+   between them) race on it and must not be issued.
    Errors: MM_ERR_INVALID (as mm_fine_propagate; host or unaligned array;
    scratch needed above MM_NOALLOC_SCRATCH_BYTES, with the size in the
    message), MM_ERR_UNSTABLE, MM_ERR_CUDA. */
@@ -258,8 +262,9 @@ typedef struct {
    of every shape that suits the context -- the resident kernel with each
    cluster size 1, 2, 4, 8 its rules allow, the streaming kernel with each
    lane layout (8, 4, 2 or 1 velocity nodes per lane in FP32; 4, 2, 1 in
-   FP64) -- restricted by params.fine_kernel when that is not 0, and keeps
-   the fastest for every later mm_fine_propagate and parareal_run of this
+   FP64, or 8 where 4 needs more than 32 lanes) -- restricted by
+   params.fine_kernel when that is not 0, and keeps the fastest for every
+   later mm_fine_propagate and parareal_run of this
    context (mm_query reports it).  The batch engine's work-list kernel is
    not affected.
      rho_in, g_in   inputs as for mm_fine_propagate (not modified)
@@ -348,6 +353,36 @@ MM_API mm_status parareal_run(mm_ctx* ctx, const mm_parareal_cfg* cfg,
                        const double* rho0, const void* g0,
                        double* rho_slices_out, mm_parareal_stats* stats,
                        void* stream);
+
+/* Algorithm 1's sequential parts as separate calls (Sec. 3.3), for a driver
+   that spreads the fine propagations of an iteration over several devices:
+   each device runs F (mm_lift, mm_fine_propagate) on its block of the
+   slices n = k..N-1, the F results are gathered on every device, and every
+   device then runs the same correction, so all of them hold the same
+   iterate.  The arithmetic is parareal_run's (same kernels); the per-slice
+   fine propagations do not depend on how the slices are split.  Arrays are
+   device pointers; rho_bar NaN takes the mean of slice 0 (a host read).
+
+   mm_coarse_guess: the coarse guess rho^{n+1,0} = G(rho^{n,0}),
+   n = 0..N-1, with G = S^0 over t_span (mm_coarse's propagator).
+     rho_slices [N+1][nx] double: slice 0 given, slices 1..N written
+     g_prev     [N+1][nx] double: G(rho^{n,0}) written at index n+1
+   Errors: MM_ERR_INVALID (sizes, NULL or host arrays), MM_ERR_CUDA,
+   MM_ERR_OOM. */
+MM_API mm_status mm_coarse_guess(mm_ctx* ctx, int32_t n_slices, double t_span, double* rho_slices,
+                                 double* g_prev, void* stream);
+
+/* mm_parareal_correct: the sequential correction of iteration k,
+   rho^{n+1,k+1} = G(rho^{n,k+1}) + F(rho^{n,k}) - G(rho^{n,k}) for
+   n = k..N-1 in order, g_prev[n+1] <- G(rho^{n,k+1}), and the successive
+   error max_{n,i} |rho^{n,k+1} - rho^{n,k}| into err[0] (device double).
+     rho_slices [N+1][nx] in/out; f_rho [N+1][nx], F(rho^{n,k}) at index
+     n+1 for n = k..N-1; g_prev [N+1][nx] in/out.
+   Errors: MM_ERR_INVALID (k outside [0, N), NULL or host arrays),
+   MM_ERR_CUDA, MM_ERR_OOM. */
+MM_API mm_status mm_parareal_correct(mm_ctx* ctx, int32_t n_slices, int32_t k, double t_span,
+                                     double* rho_slices, const double* f_rho, double* g_prev, double* err,
+                                     void* stream);
 
 /* --------------------------------------------------------- many solves --- */
 

@@ -243,14 +243,23 @@ static bool layout_for(int nv, int vpt, mmk::LaneLayout* out) {
   return true;
 }
 
-static const int kVpt32[] = {8, 4, 2, 1}, kVpt64[] = {4, 2, 1};
+static const int kVpt32[] = {8, 4, 2, 1}, kVpt64[] = {4, 2, 1, 8};
+
+// Whether the streaming kernel offers vpt nodes per lane for this nv and
+// precision.  FP64 takes 8 nodes per lane only where 4 would need more than
+// 32 lanes (nv = 256): 8 doubles per lane cost registers the other layouts
+// keep.
+static bool vpt_offered(int nv, bool fp32, int vpt, mmk::LaneLayout* out) {
+  mmk::LaneLayout l4;
+  if (!fp32 && vpt == 8 && layout_for(nv, 4, &l4)) return false;
+  return layout_for(nv, vpt, out);
+}
 
 // Default layout: the most velocity nodes per lane that works.
 static bool choose_layout(int nv, bool fp32, mmk::LaneLayout* out) {
   const int* c = fp32 ? kVpt32 : kVpt64;
-  const int nc = fp32 ? 4 : 3;
-  for (int q = 0; q < nc; ++q)
-    if (layout_for(nv, c[q], out)) return true;
+  for (int q = 0; q < 4; ++q)
+    if (vpt_offered(nv, fp32, c[q], out)) return true;
   return false;
 }
 
@@ -272,9 +281,8 @@ static mm_status validate(const mm_params* p) {
   if (p->fine_kernel < 0 || p->fine_kernel > 2) return mm_fail(MM_ERR_INVALID, "fine_kernel must be 0, 1 or 2");
   if (p->fine_vpt != 0) {
     mmk::LaneLayout l;
-    const int mx = p->precision == MM_FP32G ? 8 : 4;
-    if (p->fine_vpt < 0 || p->fine_vpt > mx || (p->fine_vpt & (p->fine_vpt - 1)) ||
-        !layout_for(p->nv, p->fine_vpt, &l))
+    if (p->fine_vpt < 0 || p->fine_vpt > 8 || (p->fine_vpt & (p->fine_vpt - 1)) ||
+        !vpt_offered(p->nv, p->precision == MM_FP32G, p->fine_vpt, &l))
       return mm_fail(MM_ERR_INVALID, "fine_vpt: no lane layout with that many nodes per lane for this nv");
   }
   if (p->fine_kernel == 2) {
@@ -338,6 +346,13 @@ extern "C" mm_status mm_create(const mm_params* p, const mm_alloc* alloc, mm_ctx
     cudaStreamSynchronize(0);
     delete c;
     return mm_cuda_fail(e, "mm_create: velocity table");
+  }
+  // everything mm_fine_propagate_noalloc needs from the device is reserved
+  // here, so that its calls allocate nothing
+  if ((st = mmk::noalloc_setup(c)) != MM_OK) {
+    mmk::ctx_release(c, 0);
+    cudaStreamSynchronize(0);
+    return st;
   }
   *out = c;
   return MM_OK;
@@ -609,10 +624,10 @@ extern "C" mm_status mm_autotune(mm_ctx* c, int32_t batch, int32_t steps, const 
       if (mmk::fine_resident_smem(p.nx, p.nv, fp32, adapt, p.flux_rule, C)) cands.push_back({2, C, c->lay, 0.0});
   if (p.fine_kernel != 2) {
     const int* vp = fp32 ? kVpt32 : kVpt64;
-    for (int q = 0; q < (fp32 ? 4 : 3); ++q) {
+    for (int q = 0; q < 4; ++q) {
       mmk::LaneLayout lay;
       if (p.fine_vpt && vp[q] != p.fine_vpt) continue;
-      if (layout_for(p.nv, vp[q], &lay)) cands.push_back({1, 0, lay, 0.0});
+      if (vpt_offered(p.nv, fp32, vp[q], &lay)) cands.push_back({1, 0, lay, 0.0});
     }
   }
   if (cands.empty()) return mm_fail(MM_ERR_INVALID, "mm_autotune: no launch shape suits this context");
@@ -1003,34 +1018,105 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
 // Kernel arguments of F for one call, with every buffer pointer left unset
 // (used by the entry point that takes its scratch from static device
 // memory instead of the workspace).
-mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out) {
+// ------------------------------------------- parareal building blocks --
+
+// Algorithm 1's sequential parts as separate calls, for drivers that run
+// the fine propagations of one iteration on several devices (each device
+// its block of slices, the results gathered, the sequential part redone on
+// every device).  Device arrays only.
+static mm_status parareal_rb(mm_ctx* c, const double* rho_slices, cudaStream_t s, double* rb) {
+  *rb = c->p.rho_bar;
+  if (isnan(*rb)) {
+    bool ok;
+    *rb = host_mean(rho_slices, c->p.nx, s, &ok);
+    if (!ok) return mm_fail(MM_ERR_CUDA, "parareal: reading slice 0");
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_coarse_guess(mm_ctx* c, int32_t n_slices, double t_span, double* rho_slices,
+                                     double* g_prev, void* stream) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (n_slices < 1 || !(t_span > 0)) return mm_fail(MM_ERR_INVALID, "n_slices must be >= 1 and t_span > 0");
+  if (!rho_slices || !g_prev) return mm_fail(MM_ERR_INVALID, "NULL array");
+  if (!is_device_ptr(rho_slices) || !is_device_ptr(g_prev))
+    return mm_fail(MM_ERR_INVALID, "mm_coarse_guess takes device arrays");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  double rb;
+  mm_status st = parareal_rb(c, rho_slices, s, &rb);
+  if (st != MM_OK) return st;
+  mmk::MacroArgs ma = macro_args(c, 1, t_span, rb);
+  void* gws = nullptr;
+  const size_t wsb = mmk::macro_ws_bytes(c->p.nx, std::max((int)n_slices, 1));
+  if (wsb && (st = c->ws.get(WS_MACRO, wsb, s, &gws)) != MM_OK) return st;
+  const cudaError_t e = mmk::launch_coarse_chain(ma, n_slices, rho_slices, g_prev, (double*)gws, s);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
+  return MM_OK;
+}
+
+extern "C" mm_status mm_parareal_correct(mm_ctx* c, int32_t n_slices, int32_t k, double t_span,
+                                         double* rho_slices, const double* f_rho, double* g_prev,
+                                         double* err, void* stream) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (n_slices < 1 || k < 0 || k >= n_slices || !(t_span > 0))
+    return mm_fail(MM_ERR_INVALID, "need n_slices >= 1, 0 <= k < n_slices and t_span > 0");
+  if (!rho_slices || !f_rho || !g_prev || !err) return mm_fail(MM_ERR_INVALID, "NULL array");
+  if (!is_device_ptr(rho_slices) || !is_device_ptr(f_rho) || !is_device_ptr(g_prev) || !is_device_ptr(err))
+    return mm_fail(MM_ERR_INVALID, "mm_parareal_correct takes device arrays");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  double rb;
+  mm_status st = parareal_rb(c, rho_slices, s, &rb);
+  if (st != MM_OK) return st;
+  void* gws = nullptr;
+  const size_t wsb = mmk::macro_ws_bytes(c->p.nx, std::max((int)n_slices, 1));
+  if (wsb && (st = c->ws.get(WS_MACRO, wsb, s, &gws)) != MM_OK) return st;
+  mmk::CorrectArgs ca{};
+  ca.m = macro_args(c, 1, t_span, rb);
+  ca.n_slices = n_slices;
+  ca.k = k;
+  ca.rho = rho_slices;
+  ca.frho = f_rho;
+  ca.gprev = g_prev;
+  ca.err = err;
+  const cudaError_t e = mmk::launch_correct(ca, (double*)gws, s);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
+  return MM_OK;
+}
+
+mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out, bool check_dt) {
   if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
   if (batch < 0) return mm_fail(MM_ERR_INVALID, "batch must be >= 0");
   if (!(t_span > 0)) return mm_fail(MM_ERR_INVALID, "t_span must be > 0");
-  if (c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
+  if (check_dt && c->p.dt > 0 && c->p.dt > stability_guard(c) * (1.0 + 1e-12))
     return mm_fail(MM_ERR_UNSTABLE, "params.dt is above the stability limit");
   const mm_params& p = c->p;
   const int64_t n = steps_for(t_span, c->dt_limit);
   const double dt = t_span / n;
+  const FineChoice fc = fine_choice(c);
   FinePlan f{};
   f.device = c->device;
   f.fp32 = p.precision == MM_FP32G;
-  f.vpt = c->lay.vpt;
+  f.vpt = fc.lay.vpt;
+  f.kernel = fc.kernel;
+  f.res_C = fc.kernel == 2 ? fc.C : 0;
+  f.res_smem = fc.kernel == 2 ? fc.res_smem : 0;
   f.n_steps = n;
   f.g_bytes = (size_t)batch * p.nx * p.nv * (f.fp32 ? 4 : 8);
   f.rho_bytes = (size_t)batch * p.nx * 8;
   const bool adapt = p.adapt != 0;
-  f.col_bytes = mmk::fine_column_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, false);
+  f.col_bytes = mmk::fine_column_bytes(p.nx, p.nv, fc.lay.lanes, f.fp32, adapt, false);
   f.col_in_smem = f.col_bytes == 0;
-  f.smem = mmk::fine_smem_bytes(p.nx, p.nv, c->lay.lanes, f.fp32, adapt, false);
+  f.smem = mmk::fine_smem_bytes(p.nx, p.nv, fc.lay.lanes, f.fp32, adapt, false);
   FineArgs& a = f.args;
   a.nx = p.nx;
   a.nv = p.nv;
   a.batch = batch;
   a.n_steps = n;
-  a.lanes = c->lay.lanes;
-  a.nh = c->lay.nh;
-  a.nhp = c->lay.nhp;
+  a.lanes = fc.lay.lanes;
+  a.nh = fc.lay.nh;
+  a.nhp = fc.lay.nhp;
   a.dt = dt;
   a.dx = p.x_len / p.nx;
   a.inv_dx = 1.0 / a.dx;

@@ -1112,8 +1112,9 @@ __global__ void __launch_bounds__(kFineThreads, 1)
 
 // ---------------------------------------------------------------- launch --
 
+// dry: configure (and so load) the instance without launching it.
 template <class G, int VPT, bool ADAPT, int NXC = 0, int NVC = 0>
-static cudaError_t launch_t(const FineArgs& a, size_t smem, cudaStream_t s) {
+static cudaError_t launch_t(const FineArgs& a, size_t smem, cudaStream_t s, bool dry) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(fine_kernel<G, VPT, ADAPT, NXC, NVC>,
@@ -1121,6 +1122,7 @@ static cudaError_t launch_t(const FineArgs& a, size_t smem, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  if (dry) return cudaSuccess;
   fine_kernel<G, VPT, ADAPT, NXC, NVC><<<a.batch, kFineThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -1129,12 +1131,13 @@ static cudaError_t launch_t(const FineArgs& a, size_t smem, cudaStream_t s) {
 // Nx = 4096 and Nv = 128 (the hybrid-adaptation grid); every other shape
 // takes the runtime-shape kernel.
 template <class G, int VPT>
-static cudaError_t launch_v(const FineArgs& a, size_t smem, cudaStream_t s) {
+static cudaError_t launch_v(const FineArgs& a, size_t smem, cudaStream_t s, bool dry) {
   if constexpr (sizeof(G) == 4 && VPT == 8) {
     if (a.nx == 4096 && a.nv == 128)
-      return a.adapt ? launch_t<G, VPT, true, 4096, 128>(a, smem, s) : launch_t<G, VPT, false, 4096, 128>(a, smem, s);
+      return a.adapt ? launch_t<G, VPT, true, 4096, 128>(a, smem, s, dry)
+                     : launch_t<G, VPT, false, 4096, 128>(a, smem, s, dry);
   }
-  return a.adapt ? launch_t<G, VPT, true>(a, smem, s) : launch_t<G, VPT, false>(a, smem, s);
+  return a.adapt ? launch_t<G, VPT, true>(a, smem, s, dry) : launch_t<G, VPT, false>(a, smem, s, dry);
 }
 
 template <class G, int VPT, bool ADAPT>
@@ -1156,24 +1159,34 @@ cudaError_t launch_fine_list(const FineList& L, bool fp32, bool adapt, size_t sm
   return adapt ? launch_list_t<double, 4, true>(L, smem, s) : launch_list_t<double, 4, false>(L, smem, s);
 }
 
-cudaError_t launch_fine(const FineArgs& args, int vpt, bool fp32, size_t smem, cudaStream_t s) {
+static cudaError_t fine_dispatch(const FineArgs& args, int vpt, bool fp32, size_t smem, cudaStream_t s,
+                                 bool dry) {
   FineArgs a = args;
   fine_args_floats(a);
   if (fp32) {
     switch (vpt) {
-      case 1: return launch_v<float, 1>(a, smem, s);
-      case 2: return launch_v<float, 2>(a, smem, s);
-      case 4: return launch_v<float, 4>(a, smem, s);
-      case 8: return launch_v<float, 8>(a, smem, s);
+      case 1: return launch_v<float, 1>(a, smem, s, dry);
+      case 2: return launch_v<float, 2>(a, smem, s, dry);
+      case 4: return launch_v<float, 4>(a, smem, s, dry);
+      case 8: return launch_v<float, 8>(a, smem, s, dry);
     }
   } else {
     switch (vpt) {
-      case 1: return launch_v<double, 1>(a, smem, s);
-      case 2: return launch_v<double, 2>(a, smem, s);
-      case 4: return launch_v<double, 4>(a, smem, s);
+      case 1: return launch_v<double, 1>(a, smem, s, dry);
+      case 2: return launch_v<double, 2>(a, smem, s, dry);
+      case 4: return launch_v<double, 4>(a, smem, s, dry);
+      case 8: return launch_v<double, 8>(a, smem, s, dry);
     }
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fine(const FineArgs& args, int vpt, bool fp32, size_t smem, cudaStream_t s) {
+  return fine_dispatch(args, vpt, fp32, smem, s, false);
+}
+
+cudaError_t fine_stream_preload(const FineArgs& a, int vpt, bool fp32) {
+  return fine_dispatch(a, vpt, fp32, 0, nullptr, true);
 }
 
 }  // namespace mmk

@@ -196,14 +196,28 @@ cudaError_t launch_coarse_chain_list(const CorrectArgs* list, int n, int nx_max,
 
 // Everything the fine kernel needs for one call except its buffers: the
 // arguments (pointers unset), the template choice and the byte counts.
+// The kernel and launch shape are those mm_fine_propagate would use for the
+// context (its tuned choice, else the default rule).
 struct FinePlan {
   FineArgs args;
   int device, vpt;
   bool fp32, col_in_smem;
   int64_t n_steps;
   size_t g_bytes, rho_bytes, col_bytes, smem;
+  int kernel;          // 1 streaming, 2 resident
+  int res_C;           // resident: CTAs per state
+  size_t res_smem;     // resident: dynamic shared memory
 };
-mm_status fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out);
+// check_dt: refuse a params.dt above the stability rule (MM_ERR_UNSTABLE).
+mm_status fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out, bool check_dt = true);
+// Load the kernel instances a plan launches (under lazy module loading a
+// first launch would otherwise load them, which can allocate device memory).
+cudaError_t fine_preload(const FinePlan& f);
+cudaError_t fine_stream_preload(const FineArgs& a, int vpt, bool fp32);
+// Set-up of mm_fine_propagate_noalloc for a context's device, done by
+// mm_create: the device address of the fixed scratch array, and the
+// kernels of the context's launch choice loaded.
+mm_status noalloc_setup(mm_ctx* c);
 
 // Free a context without a device-wide synchronisation (stream-ordered on s).
 void ctx_release(mm_ctx* c, cudaStream_t s);

@@ -7,17 +7,19 @@
 // memory pool, a real-time loop that must not hit the allocator's slow
 // path or an out-of-memory failure halfway through a run, or code that runs
 // where the allocator is not available to it.  They create the context once
-// at start-up (mm_create allocates its two small velocity tables there) and
-// then call this entry point as often as they like.
+// at start-up and then call this entry point as often as they like.
 //
 // The scratch is one file-scope __device__ array of MM_NOALLOC_SCRATCH_BYTES.
-// Every GPU that loads this library holds that array until the process
-// exits.  Host code cannot use the array's name as a device address (on the
-// host it names a stand-in object), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, on the
-// first call that runs on it; that first call should therefore come before
-// any stream capture.  All calls share the array: calls that overlap on the
-// GPU (different streams, no ordering between them) race on it.
+// Host code cannot use the array's name as a device address (on the host it
+// names a stand-in object), so the device address is looked up with
+// cudaGetSymbolAddress once per device, with that device current.  That
+// look-up is done by mm_create (noalloc_setup below), for the device the
+// context is created on: it loads this file's module, which reserves the
+// array on that device until the process exits, and it also loads the
+// kernels of the context's launch choice, so that under lazy module loading
+// no call of the entry point has to load (and allocate for) anything.  All
+// calls share the array: calls that overlap on the GPU (different streams,
+// no ordering between them) race on it.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -68,6 +70,29 @@ bool on_device(const void* p) {
 
 }  // namespace
 
+namespace mmk {
+
+cudaError_t fine_preload(const FinePlan& f) {
+  if (f.kernel == 2) {  // planning a launch configures (and so loads) the instance
+    resident_plan(f.args.nx, f.args.nv, 1, 1, f.res_C, f.res_smem);
+    return cudaGetLastError();
+  }
+  return fine_stream_preload(f.args, f.vpt, f.fp32);
+}
+
+mm_status noalloc_setup(mm_ctx* c) {
+  void* base;
+  mm_status st = scratch_address(ctx_device(c), &base);
+  if (st != MM_OK) return st;
+  FinePlan f;
+  if ((st = fine_plan(c, 1, 1.0, &f, false)) != MM_OK) return st;
+  const cudaError_t e = fine_preload(f);
+  if (e != cudaSuccess) return mm_cuda_fail(e, "mm_create: loading the fine kernel");
+  return MM_OK;
+}
+
+}  // namespace mmk
+
 extern "C" mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, double t_span,
                                                const double* rho_in, const void* g_in,
                                                double* rho_out, void* g_out, uint8_t* mask_out,
@@ -81,15 +106,18 @@ extern "C" mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, doubl
   }
   if (!rho_in || !g_in || !rho_out || !g_out) return mm_fail(MM_ERR_INVALID, "NULL array");
 
-  // Scratch: status word and kinetic counter, the second step buffer of g,
-  // a copy of g_in when it aliases g_out and the step count is odd (the
-  // first step would overwrite it), and the column arrays when they do not
-  // fit shared memory.
-  const bool alias = g_in == g_out && (f.n_steps & 1);
+  // Scratch: status word and kinetic counter; for the streaming kernel also
+  // the second step buffer of g, a copy of g_in when it aliases g_out and the
+  // step count is odd (the first step would overwrite it), and the column
+  // arrays when they do not fit shared memory.  The resident kernel keeps g
+  // in shared memory and carries a state from round to round in the
+  // caller's output arrays, so it needs only the status word.
+  const bool resident = f.kernel == 2;
+  const bool alias = !resident && g_in == g_out && (f.n_steps & 1);
   const size_t o_buf1 = kAlign;
-  const size_t o_copy = o_buf1 + up(f.g_bytes);
+  const size_t o_copy = o_buf1 + (resident ? 0 : up(f.g_bytes));
   const size_t o_cols = o_copy + (alias ? up(f.g_bytes) : 0);
-  const size_t need = o_cols + (f.col_in_smem ? 0 : up(f.col_bytes * (size_t)batch));
+  const size_t need = o_cols + (resident || f.col_in_smem ? 0 : up(f.col_bytes * (size_t)batch));
   if (need > MM_NOALLOC_SCRATCH_BYTES)
     return mm_fail(MM_ERR_INVALID,
                    "mm_fine_propagate_noalloc: this batch needs " + std::to_string(need) +
@@ -113,9 +141,9 @@ extern "C" mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, doubl
   a.rho_out = rho_out;
   a.g_in = g_in;
   a.g_buf0 = g_out;
-  a.g_buf1 = base + o_buf1;
+  a.g_buf1 = resident ? nullptr : base + o_buf1;
   a.mask_out = mask_out;
-  a.col_ws = f.col_in_smem ? nullptr : base + o_cols;
+  a.col_ws = resident || f.col_in_smem ? nullptr : base + o_cols;
   a.status = (int*)base;
   a.kin_count = (unsigned long long*)(base + 16);
   // the status word and the counter must start at zero on every call
@@ -126,7 +154,9 @@ extern "C" mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, doubl
     if (e != cudaSuccess) return mm_cuda_fail(e, "alias copy");
     a.g_in = base + o_copy;
   }
-  e = mmk::launch_fine(a, f.vpt, f.fp32, f.smem, s);
+  int launches = 1;
+  e = resident ? mmk::launch_fine_resident(a, f.res_C, f.res_smem, s, &launches)
+               : mmk::launch_fine(a, f.vpt, f.fp32, f.smem, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
   if (stats) {
     int hs[6] = {0};
@@ -140,7 +170,7 @@ extern "C" mm_status mm_fine_propagate_noalloc(mm_ctx* ctx, int32_t batch, doubl
     stats->full_updates = f.n_steps * (int64_t)batch * a.nx * a.nv;
     stats->device_status = hs[0];
     stats->elapsed_ms = 0.0;
-    stats->launches = 1;
+    stats->launches = launches;
     if (hs[0] != 0) return mm_fail((mm_status)hs[0], "fine: non-finite density");
   }
   return MM_OK;

@@ -27,7 +27,8 @@ STATUS_NAMES = ["MM_OK", "MM_ERR_INVALID", "MM_ERR_OOM", "MM_ERR_CUDA", "MM_ERR_
                 "MM_ERR_UNSTABLE", "MM_ERR_BUSY", "MM_ERR_NOT_READY", "MM_ERR_UNKNOWN_TICKET"]
 
 EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine_propagate",
-            "mm_fine_propagate_noalloc", "mm_autotune", "mm_coarse", "mm_lift", "parareal_run", "mm_batch_footprint",
+            "mm_fine_propagate_noalloc", "mm_autotune", "mm_coarse", "mm_lift", "parareal_run", "mm_coarse_guess",
+            "mm_parareal_correct", "mm_batch_footprint",
             "mm_batch_create", "mm_batch_add", "mm_batch_step", "mm_batch_query", "mm_batch_take",
             "mm_batch_bytes", "mm_batch_counters", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
             "serve_poll", "mm_server_destroy", "mm_last_error"]
@@ -134,6 +135,9 @@ def load(build_if_missing: bool = True):
             "mm_coarse": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V]),
             "mm_lift": (ctypes.c_int, [V, ctypes.c_int32, V, V, V]),
             "parareal_run": (ctypes.c_int, [V, P(mm_parareal_cfg), V, V, V, P(mm_parareal_stats), V]),
+            "mm_coarse_guess": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V]),
+            "mm_parareal_correct": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, V, V, V,
+                                                   V, V]),
             "mm_server_create": (ctypes.c_int, [P(mm_server_cfg), P(mm_alloc), P(V)]),
             "serve_submit": (ctypes.c_int, [V, P(mm_request), P(ctypes.c_uint64)]),
             "serve_poll": (ctypes.c_int, [V, ctypes.c_uint64, P(mm_result), ctypes.c_int32]),
@@ -289,6 +293,17 @@ def parareal_run(ctx: Ctx, t_end: float, n_slices: int, max_iter: int, tol: floa
             "mass_drift": st.mass_drift, "fine_steps": st.fine_steps,
             "kinetic_updates": st.kinetic_updates, "elapsed_ms": st.elapsed_ms,
             "fine_ms": st.fine_ms, "fine_launches": st.fine_launches}
+
+
+def mm_coarse_guess(ctx: Ctx, n_slices: int, t_span: float, rho_slices, g_prev, stream=None):
+    _check(load().mm_coarse_guess(ctx.handle, n_slices, t_span, _ptr(rho_slices), _ptr(g_prev),
+                                  _stream(stream)))
+
+
+def mm_parareal_correct(ctx: Ctx, n_slices: int, k: int, t_span: float, rho_slices, f_rho, g_prev, err,
+                        stream=None):
+    _check(load().mm_parareal_correct(ctx.handle, n_slices, k, t_span, _ptr(rho_slices), _ptr(f_rho),
+                                      _ptr(g_prev), _ptr(err), _stream(stream)))
 
 
 def _stats_dict(st: "mm_parareal_stats") -> dict:

@@ -103,7 +103,8 @@ def test_every_streaming_layout_matches_oracle(prec, vpt):
 def test_fine_vpt_rejects_impossible_layouts():
     device()
     with pytest.raises(mm.MMError):
-        mm.mm_create(params(64, 32, 1.0, mm.MM_FP64, fine_vpt=8))    # FP64 holds at most 4 per lane
+        mm.mm_create(params(64, 32, 1.0, mm.MM_FP64, fine_vpt=8))    # FP64: 8 per lane only where 4 cannot
+    mm.mm_create(params(64, 256, 1.0, mm.MM_FP64, fine_vpt=8)).close()  # nv = 256: 4 per lane needs 64 lanes
     with pytest.raises(mm.MMError):
         mm.mm_create(params(64, 12, 1.0, mm.MM_FP32G, fine_vpt=4))   # nv/2 = 6 is not a multiple of 4
     with pytest.raises(mm.MMError):

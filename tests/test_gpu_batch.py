@@ -40,6 +40,17 @@ def _mixed_set():
     return out
 
 
+def _sensitivity(p, w, t_end, N, K, ref):
+    """The oracle's own change under one-ulp perturbations of rho0."""
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for _ in range(2):
+        r = w.rho0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=w.nx))
+        out, _, _ = O.parareal(oparams(p), r, w.g0, t_end, N, K)
+        worst = max(worst, rel(out, ref))
+    return worst
+
+
 def _single(p, w, t_end, N, K, tol=0.0):
     dev = device()
     ctx = mm.mm_create(p)
@@ -83,8 +94,13 @@ def test_batch_matches_single_solves_and_oracle():
         assert rel(o, single) <= tol, (p.nx, p.nv, rel(o, single))
         ref, err, it = O.parareal(oparams(p), w.rho0, w.g0, t_end, N, K)
         assert it == K
-        if p.eps < 1.0:  # at eps = 1 relifting amplifies rounding (see gpu_helpers)
-            assert rel(o, ref) <= tol, (p.nx, p.nv, rel(o, ref))
+        # slices 0 and 1 (one fine propagation of the given data) at the
+        # parity tolerance; later slices too below eps = 1, while at eps = 1
+        # relifting amplifies rounding from slice to slice (see gpu_helpers),
+        # so they are held to 20 times the oracle's own one-ulp sensitivity
+        assert rel(o[:2], ref[:2]) <= tol, (p.nx, p.nv, rel(o[:2], ref[:2]))
+        bound = tol if p.eps < 1.0 else max(tol, 20 * _sensitivity(p, w, t_end, N, K, ref))
+        assert rel(o, ref) <= bound, (p.nx, p.nv, rel(o, ref), bound)
         assert info["mass_drift"] <= 1e-12
 
 
@@ -164,3 +180,33 @@ def test_batch_rejects_bad_input():
         mm.mm_batch_take(b, 12345, None)
     assert e.value.status == mm.MM_ERR_UNKNOWN_TICKET
     b.close()
+
+
+@pytest.mark.parametrize("eps,shapes", [
+    (1e-2, [(8192, 256), (8192, 32), (128, 256)]),
+    (5e-4, [(2048, 256), (2048, 32), (128, 256)]),
+])
+def test_batch_extreme_many_solve_shapes_match_oracle(eps, shapes):
+    """The work-list kernel at the corners of the many-solve family (FP32 g,
+    adaptation on with the hybrid thresholds on eps^2 |R|), three shapes in
+    one batch, two slices of a few fine steps, one parareal iteration,
+    against the oracle's Algorithm 1 (density within 1e-5, mass drift
+    1e-12).  At eps = 1e-2 nearly every cell is kinetic, up to Nx = 8192
+    and Nv = 256; at 5e-4 the masks are mixed (67-85% kinetic).  Mixed
+    masks at Nx = 8192 are left to the FP64 path: there the remainder
+    criterion amplifies float-g rounding past its threshold (see
+    test_gpu_fine.py::test_fp64_nx8192_mixed_masks)."""
+    solves = []
+    for q, (nx, nv) in enumerate(shapes):
+        w = W.batched(nx, nv, eps, seed=W.SEED_BASE + 101 * q, n_slices=2)
+        p = params(nx, nv, eps, mm.MM_FP32G, rho_bar=1.0, adapt=1, thr_g=1e-3, thr_R=1e-2, r_scale=1)
+        ctx = mm.mm_create(p)
+        dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+        ctx.close()
+        solves.append((p, w, 2 * 6 * dt * (1 - 1e-9), 2, 1))
+    outs, infos, _ = _run_batch(solves)
+    for (p, w, t_end, N, K), o, info in zip(solves, outs, infos):
+        ref, _, it = O.parareal(oparams(p), w.rho0, w.g0, t_end, N, K)
+        assert info["iterations"] == it == 1
+        assert rel(o, ref) <= FP32_TOL, (p.nx, p.nv, rel(o, ref))
+        assert info["mass_drift"] <= 1e-12

@@ -112,6 +112,39 @@ def test_hybrid_adaptation_masks_and_density(prec, flux_rule):
     assert 0 < st["kinetic_updates"] < st["full_updates"]
 
 
+@pytest.mark.parametrize("adapt", [0, 1])
+def test_fp64_nv256(adapt):
+    """FP64 path at Nv = 256 (the many-solve family's and the large serving
+    requests' velocity grid): 8 nodes per lane, 32 lanes per column.
+    Nx=1024, eps=1e-2, 25 steps; with adaptation a mixed kinetic/fluid
+    state, identical masks and 1e-12 on the density."""
+    p, rho, g = _hybrid(mm.MM_FP64, 0, nx=1024, nv=256)
+    p.adapt = adapt
+    ctx = mm.mm_create(p)
+    q0 = mm.mm_query(ctx, 1.0)
+    ctx.close()
+    assert q0["vpt"] == 8 and q0["lanes"] == 32
+    ro, go, mo, st, q = _check(p, rho, g, 25 * q0["dt_limit"] * (1 - 1e-9))
+    if adapt:
+        assert 0 < mo.sum() < mo.size
+
+
+def test_fp64_nx8192_mixed_masks():
+    """FP64 path at the many-solve family's largest grid with mixed masks
+    (Nx = 8192, Nv = 256, eps = 5e-4, ~80% of cells kinetic, 6 steps):
+    identical masks and 1e-12.  (The FP32-g path cannot hold the masks
+    here: rounding g to float perturbs the density by ~4e-12 per step, and
+    the remainder criterion, a fourth difference over dx = 1/8192 scaled by
+    eps^2, amplifies that to ~4e-2, above thr_R = 1e-2.)"""
+    w = W.batched(8192, 256, 5e-4, n_slices=2)
+    p = params(8192, 256, 5e-4, mm.MM_FP64, rho_bar=1.0, adapt=1, thr_g=1e-3, thr_R=1e-2, r_scale=1)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    _, _, mo, _, _ = _check(p, w.rho0[None], w.g0[None], 6 * dt * (1 - 1e-9))
+    assert 0 < mo.sum() < mo.size
+
+
 def test_fp32_mass_conservation_long_window():
     """FP32-g path over 2000 steps of the batched grid: the density stays
     within 1e-12 relative mass drift (float-float density and fluxes)."""
