@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the hybrid and serving sub-records of the default line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--precision", default="fp32g", choices=["fp32g", "fp64"])
     ap.add_argument("--kernel-only", default=None, choices=["fine", "coarse"],
@@ -397,7 +399,7 @@ def run_ours(a, rank, world, dist):
 H_NX, H_NV, H_EPS, H_VMAX = 4096, 128, 1e-3, 10.0
 
 
-def run_hybrid(a):
+def run_hybrid(a, e2e_steps=None):
     """Hybrid domain adaptation: F = S^HMM with both criteria on `--states`
     slice states of Nx=4096, Nv=128 on [-10,10], eps=1e-3, FP32 g, each
     carrying a localized non-equilibrium bump 0.5 (M(v-2) - M(v)) of width
@@ -405,7 +407,9 @@ def run_hybrid(a):
     One step = one mm_fine_propagate of all states over a fixed window of
     `--window` (64) fine steps: T = 1 would need 177,769 steps per slice.
     g is 2 MiB per state (512 MiB for 256 states), far above the L2, so the
-    kernel streams g from HBM; value = kinetic cell-updates per second."""
+    kernel streams g from HBM; value = kinetic cell-updates per second.
+    Returns the JSON line (e2e_steps: host-array steps of the end-to-end
+    figure, default max(3, steps))."""
     import numpy as np
     import torch
 
@@ -453,16 +457,22 @@ def run_hybrid(a):
     kin_frac = upd / (a.steps * st["full_updates"])
     kinetic_cells = float(mask.double().mean().item())
     # end to end with host arrays (g in and out cross PCIe/C2C every step)
-    rho_h, g_h = pinned_like(rho_h), pinned_like(g_h)
-    ro_h, go_h = pinned_like(np.empty_like(rho_h)), pinned_like(np.empty_like(g_h))
-    for _ in range(2):  # first touches of the staging buffers and host pages
-        mm.mm_fine_propagate(ctx, a.states, span, rho_h, g_h, ro_h, go_h, stats=True)
-    t0 = time.perf_counter()
-    e2e_steps = max(3, a.steps)
-    e2e_upd = 0
-    for _ in range(e2e_steps):
-        e2e_upd += mm.mm_fine_propagate(ctx, a.states, span, rho_h, g_h, ro_h, go_h, stats=True)["kinetic_updates"]
-    e2e_s = time.perf_counter() - t0
+    e2e_steps = max(3, a.steps) if e2e_steps is None else e2e_steps
+    e2e = None
+    if e2e_steps > 0:
+        rho_h, g_h = pinned_like(rho_h), pinned_like(g_h)
+        ro_h, go_h = pinned_like(np.empty_like(rho_h)), pinned_like(np.empty_like(g_h))
+        for _ in range(2):  # first touches of the staging buffers and host pages
+            mm.mm_fine_propagate(ctx, a.states, span, rho_h, g_h, ro_h, go_h, stats=True)
+        t0 = time.perf_counter()
+        e2e_upd = 0
+        for _ in range(e2e_steps):
+            e2e_upd += mm.mm_fine_propagate(ctx, a.states, span, rho_h, g_h, ro_h, go_h,
+                                            stats=True)["kinetic_updates"]
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": e2e_upd / e2e_s, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": int(rho_h.nbytes + g_h.nbytes),
+               "d2h_bytes_per_step": int(ro_h.nbytes + go_h.nbytes)}
     ctx.close()
     peaks = {}
     try:
@@ -493,11 +503,8 @@ def run_hybrid(a):
                          "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "kernel": kname, "launch_ms": round(launch_ms, 3),
                          "bytes_per_update": BYTES_PER_UPDATE},
-            "e2e": {"value": e2e_upd / e2e_s, "unit": "cell-updates/s",
-                    "h2d_bytes_per_step": int(rho_h.nbytes + g_h.nbytes),
-                    "d2h_bytes_per_step": int(ro_h.nbytes + go_h.nbytes)},
-            "gpu_launches": a.steps, "clocks": clk.summary()}
-    print(json.dumps(line))
+            "e2e": e2e, "gpu_launches": a.steps, "clocks": clk.summary()}
+    return line
 
 
 # ----------------------------------------------------------- paper workload --
@@ -653,31 +660,35 @@ def run_many(a):
 
 # -------------------------------------------------------- serving workload --
 
-def run_serving(a):
-    """Serving: open-loop Poisson arrivals (`--rate` per second for
-    `--duration` s) of solves drawn as in the many-solve workload plus 5%
-    large solves (Nx=32768, Nv=256, N=512), each a parareal solve with K=2
-    on a window of `--window` fine steps per slice, FP32 g, through the
-    server (continuous batching, 150 GB admission budget).  Reports p50/p99
-    latency (submit -> result) and aggregate cell-updates/s, and beside it
-    the plain per-solve FP64 GPU path (parareal_run, FP64) on a sample of the
-    same requests run alone."""
+def run_serving(a, rate=None, duration=None, window=None, fp64_max=96):
+    """Serving: open-loop Poisson arrivals (`rate` per second for `duration`
+    s) of solves drawn as in the many-solve workload plus 5% large solves
+    (Nx=32768, Nv=256, N=512), each a parareal solve with K=2 on a window of
+    `window` fine steps per slice, FP32 g, through the server (continuous
+    batching, 150 GB admission budget).  Reports p50/p99 latency (submit ->
+    result) and aggregate cell-updates/s, and beside it the plain per-solve
+    FP64 GPU path (parareal_run, FP64, each request alone) on the same
+    requests: all of them when there are at most fp64_max, else every k-th
+    request (large ones included at their share).  Returns the JSON line."""
     import threading
 
     import numpy as np
     import torch
 
     from paper_2511_13386_gb300 import mm, workloads as W
+    rate = a.rate if rate is None else rate
+    duration = a.duration if duration is None else duration
+    window = a.window if window is None else window
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    arrivals = W.serving(rate=a.rate, duration=a.duration)
+    arrivals = W.serving(rate=rate, duration=duration)
     reqs = []
     for ar in arrivals:  # initial data built before the clock starts (FP32 g only)
         w = W.materialise(ar.workload)
         p = mm.mm_params_default(nx=w.nx, nv=w.nv, eps=w.eps, v_max=w.v_max, rho_bar=1.0, adapt=1,
                                  thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, precision=mm.MM_FP32G)
         g32 = np.ascontiguousarray(w.g0.astype(np.float32))
-        reqs.append((ar.t, ar.workload, p, _window_t_end(mm, p, w.n_slices, a.window),
+        reqs.append((ar.t, ar.workload, p, _window_t_end(mm, p, w.n_slices, window),
                      np.ascontiguousarray(w.rho0), g32))
     K = 2
     srv = mm.mm_server_create(150 * 10 ** 9, 100000, wait_limit_ms=600000)
@@ -705,10 +716,10 @@ def run_serving(a):
     lat = np.array([r["latency_ns"] for r in results]) / 1e6
     ok = sum(r["status"] == mm.MM_OK for r in results)
     upd = sum(r["kinetic_updates"] for r in results)
-    # plain per-solve FP64 path on a sample (each alone, device arrays)
-    # (the FP64 streaming kernel holds at most 32 lanes of 4 nodes: nv <= 128)
-    sample = [q for q in range(0, len(reqs), max(1, len(reqs) // 24)) if reqs[q][1].nv <= 128]
-    f_upd, f_ms = 0, 0.0
+    # the plain per-solve FP64 path on the same requests, each alone
+    stride = 1 if len(reqs) <= fp64_max else -(-len(reqs) // fp64_max)
+    sample = list(range(0, len(reqs), stride))
+    f_upd, f_ms, s_upd = 0, 0.0, 0
     for q in sample:
         t, w, p, t_end, r0, g0 = reqs[q]
         w = W.materialise(w)
@@ -721,12 +732,14 @@ def run_serving(a):
         ctx.close()
         f_upd += info["kinetic_updates"]
         f_ms += info["elapsed_ms"]
+        s_upd += results[q]["kinetic_updates"]
+    torch.cuda.empty_cache()
     line = {"metric": "cell-updates/s", "value": upd / wall, "unit": "cell-updates/s", "n_gpus": 1,
             "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / max(len(reqs), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"serving: Poisson arrivals {a.rate}/s for {a.duration} s, many-solve "
-                                   f"sizes + 5% Nx=32768 Nv=256 N=512, K={K}, {a.window} fine steps per "
+            "config": {"workload": f"serving: Poisson arrivals {rate}/s for {duration} s, many-solve "
+                                   f"sizes + 5% Nx=32768 Nv=256 N=512, K={K}, {window} fine steps per "
                                    f"slice, 150 GB budget, continuous batching",
                        "requests": len(reqs), "completed_ok": ok,
                        "large_requests": sum(1 for r in reqs if r[1].nx == 32768)},
@@ -734,9 +747,36 @@ def run_serving(a):
                            "max": float(lat.max())},
             "fp64_per_solve": {"value": f_upd / (f_ms / 1e3), "unit": "cell-updates/s",
                                "sample_requests": len(sample),
-                               "path": "parareal_run, FP64, each request alone (requests with nv <= 128)"},
+                               "sample_large_requests": sum(1 for q in sample if reqs[q][1].nx == 32768),
+                               "sample_updates_fp64": f_upd, "sample_updates_served": s_upd,
+                               "path": "parareal_run, FP64, each request alone (every nv, 256 included)"},
             "wall_s": wall, "clocks": clk.summary()}
-    print(json.dumps(line))
+    return line
+
+
+def extra_records(a):
+    """The metric's other two parts, measured in the default run beside the
+    headline: the HBM-streaming fraction of the hybrid-adaptation workload
+    (256 states of Nx=4096, Nv=128, 64 fine steps per launch, 3 timed
+    launches) and a bounded serving run (Poisson arrivals at 20 requests/s
+    for 4 s, 16 fine steps per slice) with its p50/p99 latency, beside the
+    plain per-solve FP64 path on every one of its requests."""
+    import copy
+    h = copy.copy(a)
+    h.states, h.window, h.steps, h.warmup = 256, 64, 3, 2
+    hy = run_hybrid(h, e2e_steps=0)
+    sv = run_serving(a, rate=20.0, duration=4.0, window=16, fp64_max=10 ** 9)
+    hyb = {"workload": hy["config"]["workload"], "value": hy["value"], "unit": hy["unit"],
+           "ms_per_step": hy["ms_per_step"], "steps": hy["steps"], "warmup": hy["warmup"],
+           "kinetic_update_fraction": hy["config"]["kinetic_update_fraction"],
+           "roofline": hy["roofline"], "clocks": hy["clocks"]}
+    srv = {"workload": sv["config"]["workload"], "value": sv["value"], "unit": sv["unit"],
+           "requests": sv["config"]["requests"], "completed_ok": sv["config"]["completed_ok"],
+           "large_requests": sv["config"]["large_requests"], "latency_ms": sv["latency_ms"],
+           "fp64_per_solve": sv["fp64_per_solve"],
+           "vs_fp64_per_solve": sv["value"] / sv["fp64_per_solve"]["value"],
+           "wall_s": sv["wall_s"], "clocks": sv["clocks"]}
+    return {"hybrid": hyb, "serving": srv}
 
 
 def main():
@@ -748,13 +788,13 @@ def main():
         run_paper(a)
         return
     if a.workload == "hybrid" and a.impl == "ours":
-        run_hybrid(a)
+        print(json.dumps(run_hybrid(a)))
         return
     if a.workload == "many" and a.impl == "ours":
         run_many(a)
         return
     if a.workload == "serving" and a.impl == "ours":
-        run_serving(a)
+        print(json.dumps(run_serving(a)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -834,6 +874,8 @@ def main():
         # kernels per step: coarse chain, lift, correction (K=1) and the
         # fine propagator's launches
         line["gpu_launches"] = 3 * a.steps + r["fine_launches"]
+        if world == 1 and not a.no_extra:
+            line.update(extra_records(a))
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
