@@ -35,7 +35,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NX, NV, EPS, T_END, N_SLICES = 1024, 64, 1e-2, 1.0, 128
-FLOPS_PER_UPDATE = 16       # algorithmic FP32 flops per cell-update (an FMA counts 2)
+# Algorithmic FP32 flops per cell-update (an FMA counts 2), the step of
+# eq. S^MM as printed for one (interface, v_j): upwind x difference and its
+# 1/dx (3), field flux, flux difference and 1/dv (5), X = A + B (1),
+# P = <X> (2), X - P M + J xi M (4), relaxation a g - b (...) (3), <xi g*>
+# (2): 20.  The kernel folds 1/dx, 1/dv into its constants and forms P from
+# moments of the old g it builds anyway, executing 16 of them.
+FLOPS_PER_UPDATE = 20
 BYTES_PER_UPDATE = 8        # algorithmic HBM bytes per FP32 cell-update (read g, write g)
 
 
@@ -58,7 +64,8 @@ def parse():
     ap.add_argument("--eps-list", default="1,1e-1,1e-2,1e-3,1e-4",
                     help="Knudsen numbers of the paper workload's on/off matrix")
     ap.add_argument("--states", type=int, default=256, help="slice states of the hybrid workload")
-    ap.add_argument("--workload", default="batched", choices=["batched", "hybrid", "many", "serving", "paper"],
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "hybrid", "many", "serving", "paper", "variants"],
                     help="batched (default, the headline line); hybrid: F with domain adaptation on 256 "
                          "states of Nx=4096, Nv=128 (HBM-streaming); many: 2048 independent solves of random "
                          "sizes in one batch; serving: open-loop Poisson arrivals through the server")
@@ -367,6 +374,7 @@ def run_ours(a, rank, world, dist):
     sm_mhz = clk.summary().get("sm_mhz") or 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    fp32_probe = mm.mm_probe_fp32()                       # measured FFMA rate
     achieved_flops = FLOPS_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e12
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alg_gbs = BYTES_PER_UPDATE * upd_per_launch / (fine_launch_ms / 1e3) / 1e9
@@ -381,6 +389,9 @@ def run_ours(a, rank, world, dist):
                 "unit": "TFLOP/s", "frac": round(achieved_flops / fp32_peak, 4),
                 "traffic": profiled_traffic() if q["fine_kernel"] == 2 else None,
                 "peak_source": f"FP32 FMA lanes x clock: {n_sm} SMs x 128 x 2 x {sm_mhz:.0f} MHz",
+                "flops_per_update": FLOPS_PER_UPDATE,
+                "peak_measured_ffma": round(fp32_probe, 2),
+                "frac_of_measured_ffma": round(achieved_flops / fp32_probe, 4),
                 "kernel": kname, "launch_ms": round(fine_launch_ms, 3),
                 "launches_per_call": round(fine_n / a.steps, 2),
                 "hbm_equivalent": {"achieved_gbs": round(alg_gbs, 1), "peak_gbs": hbm_peak,
@@ -754,6 +765,58 @@ def run_serving(a, rate=None, duration=None, window=None, fp64_max=96):
     return line
 
 
+def run_variants(a):
+    """What the paper's literal variants do (Sec. 2.3 and the Remark after
+    Lemma 1; Sec. 5.2, Table 3).  (1) Mass: F with the cell-based density
+    update printed in eq. S^HMM (flux_rule 1) against one flux per
+    interface (flux_rule 0) on 64 states of the hybrid workload (Nx=4096,
+    Nv=128, eps=1e-3) over 64 fine steps: relative change of sum(rho) dx per
+    state.  (2) Convergence: Algorithm 1 on the paper's setup at eps=1e-3
+    with adaptation on (N=200, T=1, tol 1e-10, lifting of order 3), with the
+    remainder criterion on |R| (r_scale 0) and on eps^2 |R| (r_scale 1):
+    iterations and successive errors (Table 3 reports a stall at 1e-5 after
+    5 iterations for this entry)."""
+    import numpy as np
+    import torch
+
+    from paper_2511_13386_gb300 import mm, workloads as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    out = {"metric": "variants of the paper's scheme", "mass": {}, "convergence": {}}
+    w = W.hybrid(H_NX, H_NV, H_EPS, v_max=H_VMAX)
+    rho_b, g_b = w.with_batch(64)
+    rho = torch.tensor(rho_b, device=dev)
+    g = torch.tensor(g_b.astype(np.float32), device=dev)
+    dx = 1.0 / H_NX
+    m0 = rho.sum(dim=1) * dx
+    for fr in (0, 1):
+        p = mm.mm_params_default(nx=H_NX, nv=H_NV, eps=H_EPS, v_max=H_VMAX, rho_bar=1.0, adapt=1,
+                                 thr_g=w.thr_g, thr_R=w.thr_R, r_scale=w.r_scale, flux_rule=fr,
+                                 precision=mm.MM_FP32G)
+        ctx = mm.mm_create(p)
+        span = 64 * mm.mm_query(ctx, 1.0)["dt_limit"] * (1 - 1e-9)
+        ro, go = torch.empty_like(rho), torch.empty_like(g)
+        st = mm.mm_fine_propagate(ctx, 64, span, rho, g, ro, go, stats=True)
+        ctx.close()
+        d = ((ro.sum(dim=1) * dx - m0).abs() / m0.abs()).cpu().numpy()
+        out["mass"][f"flux_rule_{fr}"] = {"rel_mass_change_max": float(d.max()),
+                                          "rel_mass_change_mean": float(d.mean()),
+                                          "kinetic_update_fraction": st["kinetic_updates"] / st["full_updates"]}
+    for rs in (0, 1):
+        wp = W.paper(1e-3)
+        p = mm.mm_params_default(nx=wp.nx, nv=wp.nv, eps=1e-3, v_max=wp.v_max, x_len=wp.x_len,
+                                 rho_bar=wp.rho_bar, adapt=1, thr_g=wp.thr_g, thr_R=wp.thr_R, r_scale=rs,
+                                 lift_order=3, precision=mm.MM_FP64)
+        ctx = mm.mm_create(p)
+        o = torch.empty((wp.n_slices + 1, wp.nx), dtype=torch.float64, device=dev)
+        info = mm.parareal_run(ctx, wp.t_end, wp.n_slices, wp.n_slices, 1e-10, torch.tensor(wp.rho0, device=dev),
+                               torch.tensor(wp.g0, device=dev), o)
+        ctx.close()
+        out["convergence"][f"r_scale_{rs}"] = {"iterations": info["iterations"], "err": info["err"][:12],
+                                               "final_err": info["err"][-1] if info["err"] else None}
+    return out
+
+
 def extra_records(a):
     """The metric's other two parts, measured in the default run beside the
     headline: the HBM-streaming fraction of the hybrid-adaptation workload
@@ -789,6 +852,9 @@ def main():
         return
     if a.workload == "hybrid" and a.impl == "ours":
         print(json.dumps(run_hybrid(a)))
+        return
+    if a.workload == "variants" and a.impl == "ours":
+        print(json.dumps(run_variants(a)))
         return
     if a.workload == "many" and a.impl == "ours":
         run_many(a)
@@ -846,9 +912,12 @@ def main():
         import oracle
         oracle.build()
         rate, n_steps, el = cpu_oracle_rate(a.cpu_seconds, cores, pool)
+        rate1, n1, el1 = cpu_oracle_rate(a.cpu_seconds / 2, 1, None)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"oracle F on {cores} slice states of this workload (one process per core), "
-                         f"{n_steps} fine steps each ({n_steps / 7112:.2f} slices' worth), {el:.1f} s"}
+                         f"{n_steps} fine steps each ({n_steps / 7112:.2f} slices' worth), {el:.1f} s",
+               "one_core": {"value": rate1, "cores": 1,
+                            "sample": f"oracle F on one slice state, {n1} fine steps, {el1:.1f} s"}}
     if pool:
         pool.close()
 

@@ -497,6 +497,14 @@ MM_API mm_status serve_poll(mm_server* s, uint64_t ticket, mm_result* res,
 /* Stop the scheduler, fail queued requests, free device state. */
 MM_API mm_status mm_server_destroy(mm_server* s);
 
+/* Measurement helper, not part of the method: the FP32 FMA rate of the
+   current device in TFLOP/s (an FMA counts two flops), from independent FMA
+   chains on every SM timed with events on `stream` (about 4 ms; synchronises
+   the stream).  It is the measured denominator of the resident fine
+   kernel's roofline, which is bound by FP32 issue rather than by HBM.
+   Errors: MM_ERR_INVALID (NULL), MM_ERR_CUDA. */
+MM_API mm_status mm_probe_fp32(double* tflops, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 MM_API const char* mm_last_error(void);
 

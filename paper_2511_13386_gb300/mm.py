@@ -31,7 +31,7 @@ EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine
             "mm_parareal_correct", "mm_batch_footprint",
             "mm_batch_create", "mm_batch_add", "mm_batch_step", "mm_batch_query", "mm_batch_take",
             "mm_batch_bytes", "mm_batch_counters", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
-            "serve_poll", "mm_server_destroy", "mm_last_error"]
+            "serve_poll", "mm_server_destroy", "mm_probe_fp32", "mm_last_error"]
 
 
 class MMError(RuntimeError):
@@ -143,6 +143,7 @@ def load(build_if_missing: bool = True):
             "serve_poll": (ctypes.c_int, [V, ctypes.c_uint64, P(mm_result), ctypes.c_int32]),
             "mm_server_destroy": (ctypes.c_int, [V]),
             "mm_last_error": (ctypes.c_char_p, []),
+            "mm_probe_fp32": (ctypes.c_int, [P(ctypes.c_double), V]),
             "mm_batch_footprint": (ctypes.c_size_t, [P(mm_params), P(mm_parareal_cfg)]),
             "mm_batch_create": (ctypes.c_int, [P(mm_alloc), P(V)]),
             "mm_batch_add": (ctypes.c_int, [V, P(mm_params), P(mm_parareal_cfg), V, V, P(ctypes.c_uint64)]),
@@ -161,6 +162,13 @@ def load(build_if_missing: bool = True):
             f.argtypes = args
         _lib = lib
         return lib
+
+
+def mm_probe_fp32(stream=None) -> float:
+    """Measured FP32 FMA rate of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load().mm_probe_fp32(ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def mm_last_error() -> str:
@@ -203,6 +211,81 @@ def mm_params_default(**overrides) -> mm_params:
     return p
 
 
+# ------------------------------------------------------------ allocators --
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator:
+    """Device-memory callbacks handed to the library (the mm_alloc of
+    include/mm.h).  alloc(nbytes, stream) returns a device address (0 to
+    refuse, which the library reports as MM_ERR_OOM); free(ptr, stream)
+    releases one.  The library may call them from its own threads (the
+    server's schedulers); exceptions are turned into a refusal.  The object
+    must outlive every context, batch or server created with it."""
+
+    def __init__(self, alloc, free):
+        self._alloc, self._free = alloc, free
+
+        def a(n, stream, user):
+            try:
+                return int(self._alloc(int(n), stream or 0) or 0)
+            except Exception:
+                return 0
+
+        def f(ptr, stream, user):
+            try:
+                if ptr:
+                    self._free(int(ptr), stream or 0)
+            except Exception:
+                pass
+        self._cb_a, self._cb_f = _ALLOC_FN(a), _FREE_FN(f)
+        self.struct = mm_alloc(ctypes.cast(self._cb_a, ctypes.c_void_p),
+                               ctypes.cast(self._cb_f, ctypes.c_void_p), None)
+
+
+_torch_alloc = None
+
+
+def torch_allocator():
+    """The torch caching allocator as the library's device memory: workspace
+    and batch arrays come out of (and go back to) torch's pool, on the
+    stream the library passes."""
+    global _torch_alloc
+    if _torch_alloc is None:
+        import torch
+
+        def alloc(n, stream):
+            return torch.cuda.caching_allocator_alloc(n, device=torch.cuda.current_device(), stream=stream)
+
+        def free(ptr, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+        _torch_alloc = Allocator(alloc, free)
+    return _torch_alloc
+
+
+def _default_alloc():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch_allocator()
+    except Exception:
+        pass
+    return None
+
+
+def _alloc_arg(alloc):
+    """alloc: "torch" (torch's caching allocator, the default when CUDA is
+    available), None (the library's own stream-ordered cudaMallocAsync) or
+    an Allocator."""
+    if isinstance(alloc, str):
+        if alloc != "torch":
+            raise ValueError(f"unknown allocator {alloc!r}")
+        alloc = _default_alloc()
+    return (ctypes.byref(alloc.struct) if alloc is not None else None), alloc
+
+
 class Ctx:
     """Owning handle of an mm_ctx."""
 
@@ -219,10 +302,13 @@ class Ctx:
             self.handle = None
 
 
-def mm_create(params: mm_params) -> Ctx:
+def mm_create(params: mm_params, alloc="torch") -> Ctx:
     h = ctypes.c_void_p()
-    _check(load().mm_create(ctypes.byref(params), None, ctypes.byref(h)))
-    return Ctx(h, params)
+    ref, keep = _alloc_arg(alloc)
+    _check(load().mm_create(ctypes.byref(params), ref, ctypes.byref(h)))
+    c = Ctx(h, params)
+    c.alloc = keep
+    return c
 
 
 def mm_destroy(ctx: Ctx):
@@ -334,10 +420,13 @@ def mm_batch_footprint(params: mm_params, t_end: float, n_slices: int, max_iter:
     return load().mm_batch_footprint(ctypes.byref(params), ctypes.byref(cfg))
 
 
-def mm_batch_create() -> Batch:
+def mm_batch_create(alloc="torch") -> Batch:
     h = ctypes.c_void_p()
-    _check(load().mm_batch_create(None, ctypes.byref(h)))
-    return Batch(h)
+    ref, keep = _alloc_arg(alloc)
+    _check(load().mm_batch_create(ref, ctypes.byref(h)))
+    b = Batch(h)
+    b.alloc = keep
+    return b
 
 
 def mm_batch_add(batch: Batch, params: mm_params, t_end: float, n_slices: int, max_iter: int, tol: float,
@@ -408,11 +497,15 @@ class Server:
         self.close()
 
 
-def mm_server_create(hbm_budget_bytes: int, max_slots: int, wait_limit_ms: int = 60000) -> Server:
+def mm_server_create(hbm_budget_bytes: int, max_slots: int, wait_limit_ms: int = 60000,
+                     alloc="torch") -> Server:
     cfg = mm_server_cfg(hbm_budget_bytes, max_slots, wait_limit_ms)
     h = ctypes.c_void_p()
-    _check(load().mm_server_create(ctypes.byref(cfg), None, ctypes.byref(h)))
-    return Server(h)
+    ref, keep = _alloc_arg(alloc)
+    _check(load().mm_server_create(ctypes.byref(cfg), ref, ctypes.byref(h)))
+    srv = Server(h)
+    srv.alloc = keep
+    return srv
 
 
 def serve_submit(server: Server, params: mm_params, t_end: float, n_slices: int, max_iter: int,

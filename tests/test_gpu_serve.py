@@ -114,3 +114,42 @@ def test_short_requests_do_not_wait_behind_a_long_one():
     solo = [_run_batch([s])[0][0][-1] for s in solves]
     for q, r in enumerate(res):
         assert np.array_equal(r["rho_T"], solo[q]), q
+
+
+def test_serving_refused_allocation_fails_alone():
+    """Device memory comes from the caller's allocator (here torch's caching
+    allocator behind a wrapper that refuses every request of one size, the
+    slice arrays of one marked solve: Nx=64, N=13, (N+1) x 64 doubles =
+    7,168 bytes).  The marked request fails alone with MM_ERR_OOM; every
+    other request of the mix completes with its solo result, bit for bit."""
+    device()
+    base = mm.torch_allocator()
+    refused = []
+
+    def alloc(n, stream):
+        if n == 14 * 64 * 8:
+            refused.append(n)
+            return 0
+        return base._alloc(n, stream)
+
+    picky = mm.Allocator(alloc, base._free)
+    nx, nv, N = 64, 32, 13
+    wm = W.batched(nx, nv, 1e-1, seed=W.SEED_BASE + 4242, n_slices=N)
+    pm = mm.mm_params_default(nx=nx, nv=nv, eps=1e-1, precision=mm.MM_FP32G, rho_bar=1.0)
+    ctx = mm.mm_create(pm)
+    t_m = N * 5 * mm.mm_query(ctx, 1.0)["dt_limit"] * (1 - 1e-9)
+    ctx.close()
+    solves = _mixed_set()
+    solves.insert(2, (pm, wm, t_m, N, 2))
+    srv = mm.mm_server_create(1 << 40, 64, wait_limit_ms=60000, alloc=picky)
+    tickets = [mm.serve_submit(srv, p, t, n, k, 0.0, np.ascontiguousarray(w.rho0), _host_g0(p, w))
+               for (p, w, t, n, k) in solves]
+    res = [mm.serve_poll(srv, tk, w.nx, timeout_ms=60000) for tk, (p, w, *_r) in zip(tickets, solves)]
+    srv.close()
+    assert refused
+    for q, r in enumerate(res):
+        if q == 2:
+            assert r["status"] == mm.MM_ERR_OOM
+            continue
+        assert r["status"] == mm.MM_OK, q
+        assert np.array_equal(r["rho_T"], _run_batch([solves[q]])[0][0][-1]), q
