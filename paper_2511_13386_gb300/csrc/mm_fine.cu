@@ -271,7 +271,8 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return t;
 }
 
-// Block sum of float-float values (absolute-error additions).
+// Block sum of float-float values (absolute-error additions): warp sums,
+// then one warp sums the warp totals and broadcasts the result.
 __device__ __forceinline__ ff block_sum_ff(ff v, double* red) {
   for (int m = 16; m > 0; m >>= 1) v = ff_add_abs(v, ff_shfl_xor(v, m));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -279,8 +280,13 @@ __device__ __forceinline__ ff block_sum_ff(ff v, double* red) {
   __syncthreads();
   if (l == 0) r[w] = v;
   __syncthreads();
-  ff t = {0.f, 0.f};
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = ff_add_abs(t, r[q]);
+  if (w == 0) {
+    ff t = l < (int)(blockDim.x >> 5) ? r[l] : ff{0.f, 0.f};
+    for (int m = 16; m > 0; m >>= 1) t = ff_add_abs(t, ff_shfl_xor(t, m));
+    if (l == 0) r[32] = t;
+  }
+  __syncthreads();
+  const ff t = r[32];
   __syncthreads();
   return t;
 }
@@ -424,13 +430,27 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   const int nh = NHC ? NHC : A.nh, nhp = NHPC ? NHPC : A.nhp, Lg = NHPC ? 2 * NHPC : A.lanes;
   // every cell c of the state, interleaved over the block (cell c by thread
   // c mod T); unrolled when the number of rows is a constant
+  constexpr int NROW = (NXC != 0 && NXC % kFineThreads == 0) ? NXC / kFineThreads : 0;
+  int krow = -1;  // row of the cell being visited when the rows unroll (a constant per copy)
   auto cells = [&](auto&& f) {
-    if constexpr (NXC != 0 && NXC % kFineThreads == 0) {
+    if constexpr (NROW != 0) {
 #pragma unroll
-      for (int k = 0; k < NXC / kFineThreads; ++k) f(k * kFineThreads + (int)threadIdx.x);
+      for (int k = 0; k < NROW; ++k) {
+        krow = k;
+        f(k * kFineThreads + (int)threadIdx.x);
+      }
     } else {
       for (int c = threadIdx.x; c < nx; c += kFineThreads) f(c);
     }
+  };
+  // periodic neighbour c + d (|d| <= 3) of a cell visited by cells(): with
+  // unrolled rows only the first row can wrap below 0 and only the last one
+  // above nx, so the other rows index directly
+  auto nb = [&](int c, int d) {
+    if constexpr (NROW >= 3) {
+      if (d < 0 ? krow > 0 : krow < NROW - 1) return c + d;
+    }
+    return wrapi(c + d, nx);
   };
   constexpr int T = kFineThreads;
 
@@ -689,14 +709,14 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         auto Ef = [&](int c) { return ff{C.par[4 * c], C.elo[c]}; };
         ff* Jf = reinterpret_cast<ff*>(C.jd);
         const ff k1 = {A.f_k1, A.f_k1_lo};
-        auto rho_f = [&](int c) { return C.rho[wrapi(c, nx)]; };
+        auto rho_f = [&](int c, int d) { return C.rho[nb(c, d)]; };
         ff jsum = {0.f, 0.f};
         cells([&](int c) {
-          const ff e1 = ff_sub_abs(rho_f(c + 1), rho_f(c - 1));
-          const ff e2 = ff_sub_abs(rho_f(c + 2), rho_f(c - 2));
-          const ff e3 = ff_sub_abs(rho_f(c + 3), rho_f(c - 3));
+          const ff e1 = ff_sub_abs(rho_f(c, 1), rho_f(c, -1));
+          const ff e2 = ff_sub_abs(rho_f(c, 2), rho_f(c, -2));
+          const ff e3 = ff_sub_abs(rho_f(c, 3), rho_f(c, -3));
           const ff D1 = ff_mul(ff_add_abs(ff_sub_abs(ff_mul_f(e1, 45.f), ff_mul_f(e2, 9.f)), e3), k1);
-          ff Ec = ff_add_abs(Ef(wrapi(c - 1, nx)), Ef(c));
+          ff Ec = ff_add_abs(Ef(nb(c, -1)), Ef(c));
           Ec.hi *= 0.5f;
           Ec.lo *= 0.5f;
           const ff J = ff_sub_abs(D1, ff_mul(Ec, C.rho[c]));
@@ -708,9 +728,9 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         const float rbf = rb_f;
         cells([&](int c) {
           const ff J0 = Jf[c];
-          const ff Jm1 = Jf[wrapi(c - 1, nx)], Jp1 = Jf[wrapi(c + 1, nx)];
-          const ff Jm2 = Jf[wrapi(c - 2, nx)], Jp2 = Jf[wrapi(c + 2, nx)];
-          const ff Jm3 = Jf[wrapi(c - 3, nx)], Jp3 = Jf[wrapi(c + 3, nx)];
+          const ff Jm1 = Jf[nb(c, -1)], Jp1 = Jf[nb(c, 1)];
+          const ff Jm2 = Jf[nb(c, -2)], Jp2 = Jf[nb(c, 2)];
+          const ff Jm3 = Jf[nb(c, -3)], Jp3 = Jf[nb(c, 3)];
           const ff e1 = ff_sub_abs(Jp1, Jm1), e2 = ff_sub_abs(Jp2, Jm2), e3 = ff_sub_abs(Jp3, Jm3);
           const ff s1 = ff_add_abs(Jp1, Jm1), s2 = ff_add_abs(Jp2, Jm2), s3 = ff_add_abs(Jp3, Jm3);
           const ff n3 = ff_sub_abs(ff_add_abs(ff_mul_f(e1, -13.f), ff_mul_f(e2, 8.f)), e3);
@@ -720,10 +740,10 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           const float d2J = n2.hi * A.f_k2;
           const float d1J = (45.f * e1.hi - 9.f * e2.hi + e3.hi) * A.f_k1;
           const float d1r = C.par[4 * c + 2], jc = J0.hi, rc = C.rho[c].hi;
-          const float Ec = 0.5f * (C.par[4 * wrapi(c - 1, nx)] + C.par[4 * c]);
+          const float Ec = 0.5f * (C.par[4 * nb(c, -1)] + C.par[4 * c]);
           const float Rc = -d3J + Ec * d2J + (2.f * rc - 3.f * rbf) * d1J + 2.f * jc * d1r - d1r * (jc - meanJ);
           const bool big_R = A.f_rfac * fabsf(Rc) > A.f_thr_R;
-          const bool gl = C.n2[wrapi(c - 1, nx)] > A.f_thr_g2, gr = C.n2[c] > A.f_thr_g2;
+          const bool gl = C.n2[nb(c, -1)] > A.f_thr_g2, gr = C.n2[c] > A.f_thr_g2;
           uint8_t s;
           if (initial) {
             s = (gl || gr || big_R) ? 1 : 0;
@@ -838,12 +858,18 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
 
     // J and the sweep constants: E+/dv, E-/dv, P = <X>, J
     cells([&](int c) {
-      const int cl = wrapi(c - 1, nx), cr = wrapi(c + 1, nx);
+      const int cl = nb(c, -1), cr = nb(c, 1);
       G* pr = C.par + 4 * c;
       const G e = pr[0];
       const G ep = e > G(0) ? e : G(0), em = e < G(0) ? -e : G(0);
       const G pm = ((C.mp[c] - C.mp[cl]) - (C.mm[cr] - C.mm[c])) * g_inv_dx;
-      const G* en = C.ends + 4 * c;
+      G en[4];
+      if constexpr (sizeof(G) == 4) {
+        const float4 e4 = *reinterpret_cast<const float4*>(C.ends + 4 * c);
+        en[0] = e4.x; en[1] = e4.y; en[2] = e4.z; en[3] = e4.w;
+      } else {
+        for (int q = 0; q < 4; ++q) en[q] = C.ends[4 * c + q];
+      }
       const G gend = (G)0.5 * ((ep * en[2] - em * en[3]) - (ep * en[0] - em * en[1]));
       pr[2] = pm + gend;
       if constexpr (sizeof(G) == 4) {
@@ -905,11 +931,13 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       });
       const ff Fbar = ff_mul(block_sum_ff(fsum, red), Rinv_nx);  // (syncs: fluxes visible)
       const ff mdx = {-Rdx.hi, -Rdx.lo};
+      // sums of terms that are small against the density and the field:
+      // the absolute-error form (error ~2^-47 of the operands) suffices
       cells([&](int c) {
-        const int cl = wrapi(c - 1, nx);
+        const int cl = nb(c, -1);
         const ff Fl = {C.fk[cl], C.par[4 * cl + 1]}, Fc = {C.fk[c], C.par[4 * c + 1]};
-        C.rho[c] = M::sub(M::add(C.rho[c], Fl), Fc);
-        const ff E = ff_add(ff{C.par[4 * c], C.elo[c]}, ff_mul(ff_sub(Fc, Fbar), mdx));
+        C.rho[c] = ff_add_abs(C.rho[c], ff_sub_abs(Fl, Fc));
+        const ff E = ff_add_abs(ff{C.par[4 * c], C.elo[c]}, ff_mul(ff_sub_abs(Fc, Fbar), mdx));
         C.par[4 * c] = E.hi;
         C.elo[c] = E.lo;
       });
