@@ -450,22 +450,32 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
       const int i = i0 + k;
       const float4 pr = ld4(par + 4u * (i + grp));  // padded: i / R == grp
       const float ep = pr.x, em = pr.y, bP = pr.z, bJ = pr.w;
-      const float lnb = __shfl_sync(0xffffffffu, Q[VPT - 1], src_left);
-      const float rnb = __shfl_sync(0xffffffffu, Q[0], src_right);
+      // the v-flux difference -(H_{j+1/2} - H_{j-1/2}) with
+      // H_{j+1/2} = ep g_j - em g_{j+1} expands to
+      // -(ep + em) g_j + ep g_{j-1} + em g_{j+1}; at the two ends of the
+      // velocity grid the outer flux is zero, so node 0 keeps -ep g_0 and
+      // node nv-1 keeps -em g_{nv-1}, without the outer neighbour
+      const float ae = ep + em;
+      float lnb = __shfl_sync(0xffffffffu, Q[VPT - 1], src_left);
+      float rnb = __shfl_sync(0xffffffffu, Q[0], src_right);
+      if (first_lane) lnb = 0.f;
+      if (last_lane) rnb = 0.f;
+      const float c0 = first_lane ? ep : ae, c7 = last_lane ? em : ae;
       float out[VPT];
-      float Hprev = first_lane ? 0.f : __fmaf_rn(ep, lnb, -em * Q[0]);
       float ps0 = 0.f, ps1 = 0.f;  // two chains: shorter dependency latency
 #pragma unroll
       for (int q = 0; q < VPT; ++q) {
-        const float nxt = q < VPT - 1 ? Q[q < VPT - 1 ? q + 1 : q] : rnb;
-        float H = __fmaf_rn(ep, Q[q], -em * nxt);
-        if (q == VPT - 1 && last_lane) H = 0.f;
+        const float lft = q > 0 ? Q[q > 0 ? q - 1 : 0] : lnb;
+        const float rgt = q < VPT - 1 ? Q[q < VPT - 1 ? q + 1 : q] : rnb;
+        const float cq = q == 0 ? c0 : (q == VPT - 1 ? c7 : ae);
         const float u = pos ? P[q] : N[q];
-        const float K = __fmaf_rn(-bJ, xM[q], bP * Mj[q]);
-        float t = __fmaf_rn(al[q], Q[q], K);
+        float t = __fmul_rn(bP, Mj[q]);
+        t = __fmaf_rn(-bJ, xM[q], t);
+        t = __fmaf_rn(al[q], Q[q], t);
         t = __fmaf_rn(be[q], u, t);
-        t = t - (H - Hprev);
-        Hprev = H;
+        t = __fmaf_rn(-cq, Q[q], t);
+        t = __fmaf_rn(ep, lft, t);
+        t = __fmaf_rn(em, rgt, t);
         out[q] = t;
         if (q & 1) ps1 = __fmaf_rn(wv[q], t, ps1);
         else ps0 = __fmaf_rn(wv[q], t, ps0);
