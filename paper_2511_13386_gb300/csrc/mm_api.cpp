@@ -82,6 +82,23 @@ struct Workspace {
   }
 };
 
+// A pair of timing events, released on every return path.
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  explicit EventPair(bool on) {
+    if (on) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+    }
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+};
+
 enum WsSlot {
   WS_GBUF1 = 0, WS_COLS, WS_RHO_IN, WS_RHO_OUT, WS_G_IN, WS_G_OUT, WS_MASK, WS_MACRO,
   WS_STATUS, WS_PR_RHO, WS_PR_F, WS_PR_G, WS_PR_GB, WS_PR_ERR, WS_PR_GB2, WS_PR_GOLD, WS_PR_LD, WS_COUNT
@@ -522,12 +539,9 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.kin_count = (unsigned long long*)((char*)stat_mem + 16);
   CK(cudaMemsetAsync(stat_mem, 0, 64, s), "memset status");
 
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (stats) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-  }
+  EventPair ev(stats != nullptr);
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
+  if (stats) cudaEventRecord(e0, s);
   const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
   int launches = 1;
   cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s, &launches, hooks)
@@ -547,8 +561,6 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
     if (stats) {
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       unsigned long long kc;
       memcpy(&kc, (char*)hs + 16, 8);
       stats->steps = n;
@@ -807,9 +819,8 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   const int64_t nf = steps_for(span, c->dt_limit);
   const double dtf = span / nf;
 
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  EventPair ev(true);
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   cudaEventRecord(e0, s);
 
   mm_status st;
@@ -1008,8 +1019,6 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     }
     stats->mass_drift = drift;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return MM_OK;
 }
 

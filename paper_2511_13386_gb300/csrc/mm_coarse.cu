@@ -144,7 +144,9 @@ __device__ void limit_step_implicit_block(double* rho, double* E, double* cw, do
       cw[i] = cprev;
       yp = (rho[i] - l * yp) * inv;
       lp = ((i == a0 ? -lo : 0.0) - l * lp) * inv;
-      rp = ((i == b0 - 1 ? -up : 0.0) - l * rp) * inv;
+      // the right coupling enters at the chunk's last interior row only;
+      // before it the forward sweep of that column is zero
+      rp = (i == b0 - 1) ? -up * inv : 0.0;
       y[i] = yp;
       vl[i] = lp;
       vr[i] = rp;
@@ -324,19 +326,24 @@ __device__ void correct_solve(const CorrectArgs& c, const Scratch& S, double* re
   const MacroArgs& a = c.m;
   const int nx = a.nx;
   double emax = 0.0;
-  for (int n = c.k; n < c.n_slices; ++n) {
-    const double* rn = c.rho + (size_t)n * nx;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = rn[i];
+  {
+    const double* rk = c.rho + (size_t)c.k * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) S.w[i] = rk[i];
     __syncthreads();
+  }
+  for (int n = c.k; n < c.n_slices; ++n) {
+    // S.w holds rho^{n,k+1} (the previous slice's corrected density)
     coarse_block(S, a, red);
     double* out = c.rho + (size_t)(n + 1) * nx;
     const double* F = c.frho + (size_t)(n + 1) * nx;
     double* Gp = c.gprev + (size_t)(n + 1) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = F[i] + (S.w[i] - Gp[i]);
+      const double gn = S.w[i];
+      const double v = F[i] + (gn - Gp[i]);
       emax = fmax(emax, fabs(v - out[i]));
       out[i] = v;
-      Gp[i] = S.w[i];
+      Gp[i] = gn;
+      S.w[i] = v;
     }
     __syncthreads();
   }

@@ -976,28 +976,6 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   auto sweep = [&](const G* src, G* dst) {
     const int epg = (count + ngrp - 1) / ngrp;
     const int e0 = grp * epg, e1 = min(e0 + epg, count);
-    // bring the group's old columns into L2 ahead of the register ring:
-    // one bulk prefetch of the range [first - 1, last + 3] of its run
-    // (when the run is nearly contiguous; a run with a wide gap prefetches
-    // only its start), so that the ring's loads see L2 latency
-    // (bulk copies need 16-byte aligned addresses and sizes: whole columns
-    // of a multiple of 16 bytes in a 16-byte aligned buffer)
-    if (lig == 0 && e1 > e0 && (nv * (int)sizeof(G)) % 16 == 0 &&
-        (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-      const int f = ADAPT ? (int)C.list[e0] : e0, l = ADAPT ? (int)C.list[e1 - 1] : e1 - 1;
-      const int lo = max(f - 1, 0);
-      int hi = min(l + 3, nx - 1);
-      if (hi - lo > 2 * (e1 - e0) + 8) hi = min(lo + (e1 - e0) + 4, nx - 1);
-      const char* p0 = reinterpret_cast<const char*>(src + (unsigned)lo * (unsigned)nv);
-      unsigned bytes = (unsigned)(hi - lo + 1) * (unsigned)nv * (unsigned)sizeof(G);
-      while (bytes) {
-        const unsigned b = bytes > 65536u ? 65536u : bytes;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p0)), "r"(b)
-                     : "memory");
-        p0 += b;
-        bytes -= b;
-      }
-    }
     G R0[VPT], R1[VPT], R2[VPT], R3[VPT];
 #pragma unroll
     for (int k = 0; k < VPT; ++k) R0[k] = R1[k] = R2[k] = R3[k] = G(0);
