@@ -397,7 +397,8 @@ def run_ours(a, rank, world, dist):
                 "hbm_equivalent": {"achieved_gbs": round(alg_gbs, 1), "peak_gbs": hbm_peak,
                                    "frac_of_measured": round(alg_gbs / hbm_peak, 3)}}
     ctx.close()
-    autotune = {"chosen": kname, "candidates_ms_64_steps": {
+    autotune = {"chosen": kname, "chunk_entry_steps_measured": round(tune["res_entry_steps"], 2),
+                "candidates_ms_64_steps": {
         (f"resident cluster {c['cluster']}" if c["fine_kernel"] == 2 else f"streaming {c['vpt']} nodes/lane"):
             round(c["ms"], 3) for c in tune["candidates"]}}
     return {"value": value, "total_ms": total_ms, "step_ms": step_ms, "wall": wall, "autotune": autotune,
@@ -656,6 +657,14 @@ def run_many(a):
     mem = mm.mm_batch_bytes(b)
     b.close()
     items = sum(w.n_slices for w in solves)
+    fine_ms = (c1["fine_ms"] - c0["fine_ms"]) / a.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alg_gbs = BYTES_PER_UPDATE * (upd / a.steps) / (fine_ms / 1e3) / 1e9
     line = {"metric": "cell-updates/s", "value": upd / (total_ms / 1e3), "unit": "cell-updates/s", "n_gpus": 1,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -663,8 +672,15 @@ def run_many(a):
                                    f"eps 1e-4..1, N 16..256, adaptation on, {a.window} fine steps per slice; "
                                    f"one parareal iteration of every solve per step",
                        "fine_items_first_iteration": items, "resident_bytes": mem,
-                       "fine_launch_ms": (c1["fine_ms"] - c0["fine_ms"]) / a.steps,
+                       "fine_launch_ms": fine_ms,
                        "setup_s": round(setup_s, 1)},
+            "roofline": {"bound": "hbm", "achieved": round(alg_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(alg_gbs / hbm_peak, 4), "traffic": None,
+                         "kernel": "fine_list_kernel<float, 8, adapt>",
+                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "bytes_per_update": BYTES_PER_UPDATE,
+                         "note": "algorithmic bytes (8 per kinetic update) over the work-list launch; "
+                                 "small solves' step buffers stay in L2"},
             "gpu_launches": 3 * a.steps, "clocks": clk.summary()}
     print(json.dumps(line))
 

@@ -254,6 +254,8 @@ typedef struct {
   double best_ms;            /* device time of the chosen shape */
   int32_t cand_kernel[16], cand_cluster[16], cand_vpt[16];
   double cand_ms[16];
+  double res_entry_steps;    /* resident kernel chosen: measured cost of a
+                                step chunk's entry and exit, in steps */
 } mm_tune_result;
 
 /* Autotuner of F's launch shape (the numerical scheme, eq. S^HMM of
@@ -265,8 +267,13 @@ typedef struct {
    FP64, or 8 where 4 needs more than 32 lanes) -- restricted by
    params.fine_kernel when that is not 0, and keeps the fastest for every
    later mm_fine_propagate and parareal_run of this
-   context (mm_query reports it).  The batch engine's work-list kernel is
-   not affected.
+   context (mm_query reports it).  When the resident kernel wins, the
+   tuner also times one full wave of it for `steps` and for 2 `steps`
+   steps; the difference gives the cost of a step chunk's entry and exit
+   in steps, which then sets how many steps each launch runs when a batch
+   is larger than the GPU holds at once (rounds of step chunks: more
+   chunks fill the rounds better, each adds one entry and exit).  The
+   batch engine's work-list kernel is not affected.
      rho_in, g_in   inputs as for mm_fine_propagate (not modified)
      rho_out, g_out scratch outputs (must not alias the inputs); they hold
                     the last candidate's result on return

@@ -122,6 +122,7 @@ struct mm_ctx {
   int tuned_kernel = 0;       // 1 streaming, 2 resident
   int tuned_cluster = 0;      // resident: CTAs per state
   mmk::LaneLayout tuned_lay;  // streaming: lane layout
+  double res_entry = 0;       // resident: measured chunk entry cost (step-equivalents; 0: estimate)
   // second stream and events of parareal_run's overlap of Algorithm 1's
   // sequential parts with the resident kernel's rounds (created on first use)
   cudaStream_t side = nullptr;
@@ -525,6 +526,7 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.xiM = c->vg.xiM;
   a.mu3 = c->vg.mu3;
   a.lift_order = c->p.lift_order;
+  a.res_entry_steps = c->res_entry;
 
   const size_t colb = mmk::fine_column_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
   const bool in_smem = colb == 0;
@@ -613,6 +615,7 @@ extern "C" mm_status mm_autotune(mm_ctx* c, int32_t batch, int32_t steps, const 
   if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
   if (batch == 0) {  // back to the default choice
     c->tuned = 0;
+    c->res_entry = 0;
     if (out) memset(out, 0, sizeof(*out));
     return MM_OK;
   }
@@ -671,6 +674,30 @@ extern "C" mm_status mm_autotune(mm_ctx* c, int32_t batch, int32_t steps, const 
   c->tuned_kernel = cands[best].kernel;
   c->tuned_cluster = cands[best].C;
   c->tuned_lay = cands[best].lay;
+  // Steps per launch of the resident kernel: a batch larger than the GPU
+  // holds at once runs in rounds of step chunks, and the chunk count trades
+  // the rounds' fill against each chunk's entry and exit (the state's load
+  // and store, the field's prefix sum).  That entry cost is measured here,
+  // in step-equivalents, from one full wave run for `steps` and for
+  // 2 `steps` steps: t(s) = entry + s per_step.
+  if (cands[best].kernel == 2) {
+    const size_t rs = mmk::fine_resident_smem(p.nx, p.nv, fp32, adapt, p.flux_rule, cands[best].C);
+    const int wave = std::min<int>(batch, mmk::resident_capacity(p.nx, p.nv, cands[best].C, rs));
+    double t[2] = {0.0, 0.0};
+    mm_status st = MM_OK;
+    for (int k = 0; k < 2 && st == MM_OK && wave > 0; ++k) {
+      mm_fine_stats fs;
+      for (int rep = 0; rep < 2 && st == MM_OK; ++rep)
+        st = fine_impl(c, wave, (int64_t)steps * (k + 1), dt, rho_in, g_in, rho_out, g_out, nullptr, p.rho_bar, &fs,
+                       (cudaStream_t)stream);
+      t[k] = fs.elapsed_ms;
+    }
+    if (st != MM_OK) return st;
+    const double per_step = (t[1] - t[0]) / steps;
+    c->res_entry = per_step > 0 ? std::min(1000.0, std::max(0.0, (2.0 * t[0] - t[1]) / per_step)) : 0.0;
+  } else {
+    c->res_entry = 0;
+  }
   if (out) {
     memset(out, 0, sizeof(*out));
     out->n_candidates = (int32_t)cands.size();
@@ -685,6 +712,7 @@ extern "C" mm_status mm_autotune(mm_ctx* c, int32_t batch, int32_t steps, const 
       out->cand_vpt[q] = cands[q].lay.vpt;
       out->cand_ms[q] = cands[q].ms;
     }
+    out->res_entry_steps = c->res_entry;
   }
   return MM_OK;
 }
@@ -864,7 +892,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   // sequential order: every dependency is an event.
   const FineChoice fc = fine_choice(c);
   const bool can_overlap = !full && fc.kernel == 2 && wsb == 0;
-  auto plan_for = [&](int batch) { return mmk::resident_plan(nx, nv, batch, nf, fc.C, fc.res_smem); };
+  auto plan_for = [&](int batch) { return mmk::resident_plan(nx, nv, batch, nf, fc.C, fc.res_smem, c->res_entry); };
   if (can_overlap && !c->side) {
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) c->side = nullptr;
     for (cudaEvent_t& ev : c->ov)
@@ -1148,6 +1176,7 @@ mm_status mmk::fine_plan(mm_ctx* c, int32_t batch, double t_span, FinePlan* out,
   a.xiM = c->vg.xiM;
   a.mu3 = c->vg.mu3;
   a.lift_order = c->p.lift_order;
+  a.res_entry_steps = c->res_entry;
   a.col_in_smem = f.col_in_smem ? 1 : 0;
   a.col_ws_stride = f.col_in_smem ? 0 : f.col_bytes;
   *out = f;

@@ -631,22 +631,25 @@ static int resident_slots(int C, size_t smem) {
 // entry and exit per chunk (the state goes through L2 between rounds); the
 // n mod c steps left over run as one more chunk of every state.  Every
 // launch then has one step count for all its clusters.  Cost model: rounds x
-// (chunk + kChunkEntry step-equivalents); ties go to fewer chunks.
+// (chunk + E step-equivalents), with E the entry and exit cost of a chunk:
+// measured by mm_autotune on the caller's shape, else kChunkEntry; ties go
+// to fewer chunks.
 constexpr double kChunkEntry = 8.0;
-static double rounds_cost(int batch, int64_t n_steps, int slots, int c) {
+static double rounds_cost(int batch, int64_t n_steps, int slots, int c, double E) {
   const int64_t L = n_steps / c, r = n_steps % c;
   const int64_t rounds = ((int64_t)batch * c + slots - 1) / slots;
-  double cost = (double)rounds * ((double)L + kChunkEntry);
-  if (r) cost += (double)((batch + slots - 1) / slots) * ((double)r + kChunkEntry);
+  double cost = (double)rounds * ((double)L + E);
+  if (r) cost += (double)((batch + slots - 1) / slots) * ((double)r + E);
   return cost;
 }
-static int resident_chunks(int batch, int64_t n_steps, int slots) {
+static int resident_chunks(int batch, int64_t n_steps, int slots, double E) {
   if (slots <= 0 || batch <= slots) return 1;
+  if (!(E > 0)) E = kChunkEntry;
   int best = 1;
-  double best_cost = rounds_cost(batch, n_steps, slots, 1);
+  double best_cost = rounds_cost(batch, n_steps, slots, 1, E);
   const int cmax = (int)std::min<int64_t>(n_steps, 512);
   for (int c = 2; c <= cmax; ++c) {
-    const double q = rounds_cost(batch, n_steps, slots, c);
+    const double q = rounds_cost(batch, n_steps, slots, c, E);
     if (q < 0.99 * best_cost) {
       best = c;
       best_cost = q;
@@ -670,9 +673,9 @@ static cudaError_t configure_res() {
 // The launches one call makes: pass 0 runs batch x chunks items of L steps
 // in rounds of per_round0 (chunk 0 from the input), pass 1 the r steps left
 // over, batch items in rounds of per_round1.
-static ResPlan make_plan(int batch, int64_t n_steps, int slots) {
+static ResPlan make_plan(int batch, int64_t n_steps, int slots, double E) {
   ResPlan q{};
-  q.chunks = resident_chunks(batch, n_steps, slots);
+  q.chunks = resident_chunks(batch, n_steps, slots, E);
   q.L = n_steps / q.chunks;
   q.r = n_steps % q.chunks;
   const int64_t items0 = (int64_t)batch * q.chunks;
@@ -695,7 +698,7 @@ static cudaError_t launch_res(FineArgs& a, int C, size_t smem, cudaStream_t s, i
                               const ResHooks* hooks) {
   cudaError_t e0 = configure_res<LG, RC, CC>();
   if (e0 != cudaSuccess) return e0;
-  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG, RC, CC>(C, smem));
+  const ResPlan q = make_plan(a.batch, a.n_steps, resident_slots<LG, RC, CC>(C, smem), a.res_entry_steps);
   const int64_t L = q.L, r = q.r;
   if (launches) *launches = 0;
   int li = 0;  // launch index
@@ -753,16 +756,19 @@ static int plan_slots(int nx, int C, size_t smem) {
   return slots_of<LG, 0, 0>(C, smem);
 }
 
-ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem) {
-  int slots = 0;
+int resident_capacity(int nx, int nv, int C, size_t smem) {
   switch (nv / VPT) {
-    case 2: slots = plan_slots<2>(nx, C, smem); break;
-    case 4: slots = plan_slots<4>(nx, C, smem); break;
-    case 8: slots = plan_slots<8>(nx, C, smem); break;
-    case 16: slots = plan_slots<16>(nx, C, smem); break;
-    case 32: slots = plan_slots<32>(nx, C, smem); break;
+    case 2: return plan_slots<2>(nx, C, smem);
+    case 4: return plan_slots<4>(nx, C, smem);
+    case 8: return plan_slots<8>(nx, C, smem);
+    case 16: return plan_slots<16>(nx, C, smem);
+    case 32: return plan_slots<32>(nx, C, smem);
   }
-  return make_plan(batch, n_steps, slots);
+  return 0;
+}
+
+ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem, double entry_steps) {
+  return make_plan(batch, n_steps, resident_capacity(nx, nv, C, smem), entry_steps);
 }
 
 template <int LG>

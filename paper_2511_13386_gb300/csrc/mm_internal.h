@@ -67,6 +67,9 @@ struct FineArgs {
   // launch_fine_resident)
   int res_item0, res_from_input;
   int res_state0;               // res_item0 mod batch
+  // resident kernel: cost of a chunk's entry and exit in step-equivalents,
+  // as measured by mm_autotune (0: the built-in estimate)
+  double res_entry_steps;
 };
 
 // Work list of fine propagations across solves (persistent kernel).
@@ -138,7 +141,11 @@ struct ResPlan {
   int launches() const { return launches0 + launches1; }
   int final_launch(int state) const;  // the launch after which the state is final
 };
-ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem);
+// entry_steps: a chunk's entry and exit cost in step-equivalents (0: the
+// built-in estimate)
+ResPlan resident_plan(int nx, int nv, int batch, int64_t n_steps, int C, size_t smem, double entry_steps = 0.0);
+// Clusters of the resident kernel the GPU holds at once for a shape.
+int resident_capacity(int nx, int nv, int C, size_t smem);
 // Events around the launches of one call (null entries are skipped): the
 // stream waits for before[i] ahead of launch i and records after[i] behind it.
 struct ResHooks {

@@ -73,7 +73,7 @@ class mm_tune_result(ctypes.Structure):
                 ("cluster", ctypes.c_int32), ("vpt", ctypes.c_int32), ("lanes", ctypes.c_int32),
                 ("best_ms", ctypes.c_double), ("cand_kernel", ctypes.c_int32 * 16),
                 ("cand_cluster", ctypes.c_int32 * 16), ("cand_vpt", ctypes.c_int32 * 16),
-                ("cand_ms", ctypes.c_double * 16)]
+                ("cand_ms", ctypes.c_double * 16), ("res_entry_steps", ctypes.c_double)]
 
 
 MM_PARAREAL_RHO_LIFT, MM_PARAREAL_FULL_STATE = 0, 1
@@ -355,7 +355,7 @@ def mm_autotune(ctx: Ctx, batch: int, steps: int, rho_in, g_in, rho_out, g_out, 
                               _ptr(g_out), ctypes.byref(r), _stream(stream)))
     n = min(r.n_candidates, 16)
     return {"n_candidates": r.n_candidates, "fine_kernel": r.fine_kernel, "cluster": r.cluster,
-            "vpt": r.vpt, "lanes": r.lanes, "best_ms": r.best_ms,
+            "vpt": r.vpt, "lanes": r.lanes, "best_ms": r.best_ms, "res_entry_steps": r.res_entry_steps,
             "candidates": [{"fine_kernel": r.cand_kernel[q], "cluster": r.cand_cluster[q],
                             "vpt": r.cand_vpt[q], "ms": r.cand_ms[q]} for q in range(n)]}
 

@@ -122,3 +122,33 @@ def test_autotune_rejects_aliased_outputs():
     res = mm.mm_autotune(ctx, 2, 4, r, gg, ro, go)
     assert res["fine_kernel"] == 1 and res["n_candidates"] == 3   # FP64: 4, 2, 1 nodes per lane
     ctx.close()
+
+
+def test_autotune_measures_the_step_chunk_entry_cost():
+    """When the resident kernel wins, the tuner times one full wave for
+    `steps` and 2 `steps` steps and keeps the entry cost of a step chunk (in
+    steps) that sets the steps per launch of larger batches; a batch of 160
+    states (more than the GPU holds at once) then runs in rounds of chunks
+    and still matches the oracle."""
+    dev = device()
+    w = W.batched()
+    B = 160
+    rho, g, r, gg, ro, go = _arrays(w, B, dev)
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP32G, rho_bar=1.0)
+    p.fine_kernel = 2
+    ctx = mm.mm_create(p)
+    res = mm.mm_autotune(ctx, B, 32, r, gg, ro, go)
+    assert res["fine_kernel"] == 2
+    assert 0.0 < res["res_entry_steps"] < 1000.0
+    q = mm.mm_query(ctx, 1.0)
+    span = 200 * q["dt_limit"] * (1 - 1e-9)
+    st = mm.mm_fine_propagate(ctx, B, span, r, gg, ro, go, stats=True)
+    assert st["device_status"] == 0 and st["launches"] > 1
+    op = oparams(p)
+    dt = mm.mm_query(ctx, span)["dt"]
+    ro_h = ro.cpu().numpy()
+    for b in (0, B - 1):
+        r_ref, _, _, _ = O.fine(op, 200, dt, rho[b], g[b])
+        assert rel(ro_h[b], r_ref) <= FP32_TOL
+    mm.mm_autotune(ctx, 0, 1, None, None, None, None)
+    ctx.close()
