@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from paper_2511_13386_gb300 import mm, workloads as W
-from tests.gpu_helpers import FP32_TOL, FP64_TOL, device, gdtype, oparams, params, rel
+from tests.gpu_helpers import FP32_TOL, FP64_TOL, device, gdtype, oparams, params, rel, run_fine
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -133,3 +133,59 @@ def test_many_solve_batch_full_size_sampled():
             ref, _, _ = O.parareal(oparams(p), w.rho0, w.g0, t_end, w.n_slices, 1)
             assert rel(out, ref) <= FP32_TOL, (q, rel(out, ref))
     b.close()
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32G])
+def test_largest_serving_grid(prec):
+    """The large serving requests' grid (Nx = 32768, Nv = 256; 32 MiB of
+    FP32 g per state) with the hybrid workload's data (eps = 1e-3, a
+    localized bump, ~10% of the cells kinetic), adaptation on, 3 steps of
+    one state against the oracle: FP64 with identical masks, FP32 within
+    1e-5.  (On random Fourier data at this dx the remainder criterion reads
+    rounding noise: the oracle itself flips 293 of 32,768 cells under a
+    one-ulp change of its input at eps = 5e-4, so no second implementation
+    can hold its masks there.)"""
+    w = W.hybrid(nx=32768, nv=256, eps=1e-3)
+    p = params(32768, 256, 1e-3, prec, v_max=w.v_max, rho_bar=1.0, adapt=1, thr_g=w.thr_g, thr_R=w.thr_R,
+               r_scale=w.r_scale)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    ro, go, mo, st, q = run_fine(p, w.rho0[None], w.g0[None], 3 * dt * (1 - 1e-9))
+    r_ref, g_ref, m_ref, _ = O.fine(oparams(p), q["n_steps"], q["dt"], w.rho0, w.g0)
+    assert 0 < m_ref.sum() < m_ref.size
+    if prec == mm.MM_FP64:
+        assert rel(ro[0], r_ref) <= FP64_TOL, rel(ro[0], r_ref)
+        assert np.array_equal(mo[0], m_ref)
+    else:
+        assert rel(ro[0], r_ref) <= FP32_TOL, rel(ro[0], r_ref)
+        assert (mo[0] != m_ref).sum() <= 4
+    assert st["device_status"] == 0
+
+
+@pytest.mark.parametrize("prec", [mm.MM_FP64, mm.MM_FP32G])
+def test_largest_allowed_nx(prec):
+    """nx = 65536, the largest the library accepts (the write list holds
+    16-bit interface indices), Nv = 16, 4 steps of two states against the
+    oracle: FP64 with adaptation on and a mixed mask (identical masks), FP32
+    with every cell kinetic (at this dx the remainder criterion is far
+    below FP32's resolution, see the FP32 parity domain in the design
+    notes)."""
+    w = W.hybrid(nx=65536, nv=16, eps=1e-2, v_max=8.0)
+    rho, g = w.with_batch(2)
+    adapt = 1 if prec == mm.MM_FP64 else 0
+    p = params(65536, 16, 1e-2, prec, v_max=8.0, rho_bar=1.0, adapt=adapt, thr_g=1e-3, thr_R=1e-2, r_scale=1)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    ro, go, mo, st, q = run_fine(p, rho, g, 4 * dt * (1 - 1e-9))
+    op = oparams(p)
+    for b in range(2):
+        r_ref, g_ref, m_ref, _ = O.fine(op, q["n_steps"], q["dt"], rho[b], g[b])
+        if prec == mm.MM_FP64:
+            assert rel(ro[b], r_ref) <= FP64_TOL
+            assert np.array_equal(mo[b], m_ref)
+            assert 0 < m_ref.sum() < m_ref.size
+        else:
+            assert rel(ro[b], r_ref) <= FP32_TOL
+    assert st["device_status"] == 0
