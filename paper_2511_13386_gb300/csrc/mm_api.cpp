@@ -915,7 +915,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     CK(cudaEventRecord(c->ov[0], s), "overlap event");
     CK(cudaStreamWaitEvent(side, c->ov[0], 0), "overlap wait");
     e = mmk::launch_coarse_chain(ma, N - p_split + 1, (double*)rho + (size_t)(p_split - 1) * nx,
-                                 (double*)gprev + (size_t)(p_split - 1) * nx, (double*)gws, side);
+                                 (double*)gprev + (size_t)(p_split - 1) * nx, (double*)gws, side, false);
     if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
     mmk::MacroArgs la = macro_args(c, N - p_split, span, rb);
     e = mmk::launch_lift(la, (const double*)rho + (size_t)p_split * nx, (char*)gb + (size_t)p_split * G1, fp32,
@@ -998,7 +998,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       mmk::CorrectArgs c1 = ca;
       c1.n_slices = k + m_split;
       CK(cudaStreamWaitEvent(side, c->ov[2], 0), "overlap wait");
-      e = mmk::launch_correct(c1, (double*)gws, side);
+      e = mmk::launch_correct(c1, (double*)gws, side, false);
       if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
       CK(cudaEventRecord(c->ov[3], side), "overlap event");
       CK(cudaStreamWaitEvent(s, c->ov[3], 0), "overlap join");

@@ -469,12 +469,14 @@ cudaError_t launch_coarse_chain_list(const CorrectArgs* list, int n, int nx_max,
   return launch_list(coarse_chain_list_kernel, list, n, nx_max, gws, s);
 }
 
-cudaError_t launch_correct(const CorrectArgs& c, double* gws, cudaStream_t s) {
+cudaError_t launch_correct(const CorrectArgs& c, double* gws, cudaStream_t s, bool cluster) {
+  if (cluster && c.k < c.n_slices && coarse_cluster_ok(c.m)) return launch_correct_cluster(c, s);
   return launch_macro(correct_kernel, 1, c.m.nx, gws, s, c);
 }
 
 cudaError_t launch_coarse_chain(const MacroArgs& a, int n_slices, double* rho, double* gprev,
-                                double* gws, cudaStream_t s) {
+                                double* gws, cudaStream_t s, bool cluster) {
+  if (cluster && n_slices > 0 && coarse_cluster_ok(a)) return launch_coarse_chain_cluster(a, n_slices, rho, gprev, s);
   return launch_macro(coarse_chain_kernel, 1, a.nx, gws, s, a, n_slices, rho, gprev);
 }
 

@@ -193,9 +193,17 @@ struct CorrectArgs {
   double* err;          // one double: max_n,i |rho^{n,k+1} - rho^{n,k}|
   double* work;         // [nx] scratch per solve
 };
-cudaError_t launch_correct(const CorrectArgs& a, double* gws, cudaStream_t s);
+// cluster: allow the variant that spreads one solve's implicit step over a
+// thread-block cluster (mm_coarse_cluster.cu) where the shape suits it; the
+// launches that run beside the fine kernel's rounds keep the one-CTA
+// kernel, which fits on an SM the rounds leave free.
+cudaError_t launch_correct(const CorrectArgs& a, double* gws, cudaStream_t s, bool cluster = true);
 cudaError_t launch_coarse_chain(const MacroArgs& a, int n_slices, double* rho, double* gprev,
-                                double* gws, cudaStream_t s);
+                                double* gws, cudaStream_t s, bool cluster = true);
+bool coarse_cluster_ok(const MacroArgs& a);
+cudaError_t launch_coarse_chain_cluster(const MacroArgs& a, int n_slices, double* rho, double* gprev,
+                                        cudaStream_t s);
+cudaError_t launch_correct_cluster(const CorrectArgs& c, cudaStream_t s);
 // Many solves, one CTA each; `list` in device memory; scratch for nx_max.
 size_t macro_list_ws_bytes(int nx_max, int grid);
 cudaError_t launch_correct_list(const CorrectArgs* list, int n, int nx_max, double* gws, cudaStream_t s);
