@@ -336,6 +336,10 @@ typedef struct {
   double elapsed_ms;         /* device time of the whole call (events) */
   double fine_ms;            /* device time of the fine-propagator launches */
   int32_t fine_launches;     /* fine-propagator kernel launches */
+  int32_t kernel_launches;   /* every kernel launch of the call (fine, coarse
+                                guess, lifting, correction, mass sums); 0 from
+                                mm_batch_take, whose launches serve many solves
+                                at once (mm_batch_counters) */
 } mm_parareal_stats;
 
 /* Algorithm 1 (Sec. 3.3) with F = S^HMM, G = S^0 and the lifting of order
@@ -349,7 +353,9 @@ typedef struct {
    slice's own g, and g^{n+1,k+1} = F_g(U^{n,k}) + (L G rho^{n,k+1} -
    L G rho^{n,k}) (the slices' g stay on the device, 2 (N+1) nx nv values).
    rho_slices_out [n_slices + 1][nx] double receives rho^{n,K}.  The call
-   synchronises the stream once per iteration (error test).  In density mode,
+   synchronises the stream once per iteration (error test and the fine
+   launches' status), after the correction: nothing waits between the fine
+   launches and the correction.  In density mode,
    when the resident fine kernel runs a batch in rounds of step chunks, part
    of the coarse guess, the lifting and the correction runs on a second
    stream that the context owns, ordered by events against the caller's

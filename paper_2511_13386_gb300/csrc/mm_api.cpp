@@ -101,7 +101,8 @@ struct EventPair {
 
 enum WsSlot {
   WS_GBUF1 = 0, WS_COLS, WS_RHO_IN, WS_RHO_OUT, WS_G_IN, WS_G_OUT, WS_MASK, WS_MACRO,
-  WS_STATUS, WS_PR_RHO, WS_PR_F, WS_PR_G, WS_PR_GB, WS_PR_ERR, WS_PR_GB2, WS_PR_GOLD, WS_PR_LD, WS_COUNT
+  WS_STATUS, WS_PR_RHO, WS_PR_F, WS_PR_G, WS_PR_GB, WS_PR_ERR, WS_PR_GB2, WS_PR_GOLD, WS_PR_LD, WS_PR_SUM,
+  WS_COUNT
 };
 
 }  // namespace
@@ -453,10 +454,22 @@ static mm_status device_view(mm_ctx* c, int slot, const void* p, size_t bytes, b
 
 // ----------------------------------------------------------- fine (F) ---
 
+// Deferred completion of a fine call made by a driver that synchronises
+// later anyway (parareal_run): the call records the caller's timing events
+// around its launches and leaves its status word and kinetic-update counter
+// on the device, instead of waiting for the launches to end.  Waiting there
+// would hold back whatever the driver enqueues next on another stream to
+// run beside the last launches (the correction of the slices already final).
+struct FineDefer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;  // recorded around the launches (nullable)
+  void* status = nullptr;                   // device: int status, ..., u64 counter at byte 16
+  int launches = 0;
+};
+
 static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const double* rho_in,
                            const void* g_in, double* rho_out, void* g_out, uint8_t* mask_out,
                            double rho_bar, mm_fine_stats* stats, cudaStream_t s,
-                           const mmk::ResHooks* hooks = nullptr) {
+                           const mmk::ResHooks* hooks = nullptr, FineDefer* defer = nullptr) {
   const mm_params& p = c->p;
   const bool fp32 = p.precision == MM_FP32G;
   const size_t gsz = fp32 ? 4 : 8;
@@ -541,20 +554,25 @@ static mm_status fine_impl(mm_ctx* c, int32_t batch, int64_t n, double dt, const
   a.kin_count = (unsigned long long*)((char*)stat_mem + 16);
   CK(cudaMemsetAsync(stat_mem, 0, 64, s), "memset status");
 
-  EventPair ev(stats != nullptr);
-  cudaEvent_t e0 = ev.a, e1 = ev.b;
-  if (stats) cudaEventRecord(e0, s);
+  EventPair ev(stats != nullptr && !defer);
+  cudaEvent_t e0 = defer ? defer->e0 : ev.a, e1 = defer ? defer->e1 : ev.b;
+  if (e0) cudaEventRecord(e0, s);
   const size_t smem = mmk::fine_smem_bytes(p.nx, p.nv, fc.lay.lanes, fp32, adapt, false);
   int launches = 1;
   cudaError_t e = res_C ? mmk::launch_fine_resident(a, res_C, res_smem, s, &launches, hooks)
                         : mmk::launch_fine(a, fc.lay.vpt, fp32, smem, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "fine kernel launch");
-  if (stats) cudaEventRecord(e1, s);
+  if (e1) cudaEventRecord(e1, s);
 
   if (s_rout) CK(cudaMemcpyAsync(rho_out, d_rout, rbytes, cudaMemcpyDefault, s), "copy rho_out");
   if (s_gout) CK(cudaMemcpyAsync(g_out, d_gout, gbytes, cudaMemcpyDefault, s), "copy g_out");
   if (s_mask) CK(cudaMemcpyAsync(mask_out, d_mask, mbytes, cudaMemcpyDefault, s), "copy mask");
 
+  if (defer) {  // the caller reads the status after its own synchronisation
+    defer->status = stat_mem;
+    defer->launches = launches;
+    return MM_OK;
+  }
   const bool host_out = s_rout || s_gout || s_mask;
   if (stats || host_out) {
     int hs[6] = {0};
@@ -901,6 +919,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   const bool ov_ok = can_overlap && c->side && c->ov[0] && c->ov[1] && c->ov[2] && c->ov[3];
   cudaStream_t side = c->side;
 
+  int nk = 0;  // kernel launches of this call
   // coarse guess: rho^{n+1,0} = G(rho^{n,0}); with the overlap, slices
   // 1..p-1 (the first round's states) first, the rest on the second stream
   int p_split = 0;  // states of the first round, when the guess is split
@@ -910,19 +929,23 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   }
   cudaError_t e;
   if (p_split) {
+    ++nk;
     e = mmk::launch_coarse_chain(ma, p_split - 1, (double*)rho, (double*)gprev, (double*)gws, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
     CK(cudaEventRecord(c->ov[0], s), "overlap event");
     CK(cudaStreamWaitEvent(side, c->ov[0], 0), "overlap wait");
+    ++nk;
     e = mmk::launch_coarse_chain(ma, N - p_split + 1, (double*)rho + (size_t)(p_split - 1) * nx,
                                  (double*)gprev + (size_t)(p_split - 1) * nx, (double*)gws, side, false);
     if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
     mmk::MacroArgs la = macro_args(c, N - p_split, span, rb);
+    ++nk;
     e = mmk::launch_lift(la, (const double*)rho + (size_t)p_split * nx, (char*)gb + (size_t)p_split * G1, fp32,
                          (double*)gws, side);
     if (e != cudaSuccess) return mm_cuda_fail(e, "lift");
     CK(cudaEventRecord(c->ov[1], side), "overlap event");
   } else {
+    ++nk;
     e = mmk::launch_coarse_chain(ma, N, (double*)rho, (double*)gprev, (double*)gws, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "coarse guess");
   }
@@ -931,6 +954,10 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   int64_t kin_total = 0;
   double fine_ms = 0.0;
   int fine_launches = 0;
+  EventPair fev(stats != nullptr);
+  FineDefer fd;
+  fd.e0 = fev.a;
+  fd.e1 = fev.b;
   const int K = std::min(cfg->max_iter, N);
   for (int k = 0; k < K; ++k) {
     const int batch = N - k;
@@ -945,6 +972,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       const int n_lift = p_split ? p_split - 1 : N - 1;  // slices 1..n_lift here
       if (n_lift > 0) {
         mmk::MacroArgs la = macro_args(c, n_lift, span, rb);
+        ++nk;
         e = mmk::launch_lift(la, (const double*)rho + nx, (char*)gb + G1, fp32, (double*)gws, s);
       }
       if (p_split) {  // the second round needs the rest of the guess and its lifting
@@ -953,6 +981,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       }
     } else if (!full) {
       mmk::MacroArgs la = macro_args(c, batch, span, rb);
+      ++nk;
       e = mmk::launch_lift(la, (const double*)rho + (size_t)k * nx, gb, fp32, (double*)gws, s);
     }
     if (e != cudaSuccess) return mm_cuda_fail(e, "lift");
@@ -973,16 +1002,10 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
         }
       }
     }
-    mm_fine_stats fs;
     st = fine_impl(c, batch, nf, dtf, (const double*)rho + (size_t)k * nx, g_in,
-                   (double*)frho + (size_t)(k + 1) * nx, g_out, nullptr, rb, stats ? &fs : nullptr, s,
-                   use_hooks ? &hooks : nullptr);
+                   (double*)frho + (size_t)(k + 1) * nx, g_out, nullptr, rb, nullptr, s,
+                   use_hooks ? &hooks : nullptr, &fd);
     if (st != MM_OK) return st;
-    if (stats) {
-      kin_total += fs.kinetic_updates;
-      fine_ms += fs.elapsed_ms;
-      fine_launches += fs.launches;
-    }
     // sequential correction on the device (the coarse values before it are
     // kept for the full-state g correction)
     if (full) CK(cudaMemcpyAsync(gold, gprev, rowb * (N + 1), cudaMemcpyDeviceToDevice, s), "save G");
@@ -998,6 +1021,7 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       mmk::CorrectArgs c1 = ca;
       c1.n_slices = k + m_split;
       CK(cudaStreamWaitEvent(side, c->ov[2], 0), "overlap wait");
+      ++nk;
       e = mmk::launch_correct(c1, (double*)gws, side, false);
       if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
       CK(cudaEventRecord(c->ov[3], side), "overlap event");
@@ -1005,10 +1029,12 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       ca.k = k + m_split;
       ca.err = (double*)errp + 1;
     }
+    ++nk;
     e = mmk::launch_correct(ca, (double*)gws, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "correction");
     if (full) {  // g^{n+1,k+1} = F_g(U^{n,k}) + (L G rho^{n,k+1} - L G rho^{n,k}), n = k..N-1
       mmk::MacroArgs la = macro_args(c, batch, span, rb);
+      ++nk;
       e = mmk::launch_lift_diff(la, (const double*)gprev + (size_t)(k + 1) * nx,
                                 (const double*)gold + (size_t)(k + 1) * nx, (char*)gb2 + (size_t)(k + 1) * G1,
                                 fp32, (double*)ldws, s);
@@ -1016,8 +1042,21 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
       std::swap(gb, gb2);
     }
     double errs[2] = {0.0, 0.0};
+    int hs[6] = {0};
     CK(cudaMemcpyAsync(errs, errp, m_split ? 16 : 8, cudaMemcpyDeviceToHost, s), "read error");
+    CK(cudaMemcpyAsync(hs, fd.status, 24, cudaMemcpyDeviceToHost, s), "read fine status");
     CK(cudaStreamSynchronize(s), "parareal: synchronise");
+    if (hs[0] != 0) return mm_fail((mm_status)hs[0], "fine: non-finite density");
+    if (stats) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, fd.e0, fd.e1);
+      unsigned long long kc;
+      memcpy(&kc, (char*)hs + 16, 8);
+      kin_total += (int64_t)kc;
+      fine_ms += ms;
+      fine_launches += fd.launches;
+    }
+    nk += fd.launches;
     const double err = std::max(errs[0], errs[1]);
     if (stats && k < 64) stats->err[k] = err;
     ++it;
@@ -1035,17 +1074,19 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
     stats->elapsed_ms = ms;
     stats->fine_ms = fine_ms;
     stats->fine_launches = fine_launches;
-    std::vector<double> h((size_t)(N + 1) * nx);
-    CK(cudaMemcpy(h.data(), rho, rowb * (N + 1), cudaMemcpyDefault), "read slices");
-    double m0 = 0;
-    for (int i = 0; i < nx; ++i) m0 += h[i];
+    // mass of every slice, summed on the device (N + 1 doubles come back)
+    void* sums;
+    if ((st = c->ws.get(WS_PR_SUM, (size_t)(N + 1) * 8, s, &sums)) != MM_OK) return st;
+    ++nk;
+    e = mmk::launch_row_sums((const double*)rho, N + 1, nx, (double*)sums, s);
+    if (e != cudaSuccess) return mm_cuda_fail(e, "mass sums");
+    std::vector<double> m((size_t)N + 1);
+    CK(cudaMemcpyAsync(m.data(), sums, (size_t)(N + 1) * 8, cudaMemcpyDeviceToHost, s), "read mass sums");
+    CK(cudaStreamSynchronize(s), "parareal: mass sums");
     double drift = 0;
-    for (int n = 1; n <= N; ++n) {
-      double m = 0;
-      for (int i = 0; i < nx; ++i) m += h[(size_t)n * nx + i];
-      drift = std::max(drift, fabs(m - m0) / fabs(m0));
-    }
+    for (int n = 1; n <= N; ++n) drift = std::max(drift, fabs(m[n] - m[0]) / fabs(m[0]));
     stats->mass_drift = drift;
+    stats->kernel_launches = nk;
   }
   return MM_OK;
 }

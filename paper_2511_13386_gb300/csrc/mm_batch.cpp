@@ -378,6 +378,7 @@ extern "C" mm_status mm_batch_take(mm_batch* b, uint64_t id, double* rho_slices_
     stats->kinetic_updates = v.kin;
     stats->fine_ms = b->fine_ms;
     stats->fine_launches = b->fine_launches;
+    stats->kernel_launches = 0;  // the engine's launches serve many solves (mm_batch_counters)
   }
   b->release(v, 0);
   b->solves.erase(it);

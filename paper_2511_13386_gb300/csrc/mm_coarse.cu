@@ -469,6 +469,27 @@ cudaError_t launch_coarse_chain_list(const CorrectArgs* list, int n, int nx_max,
   return launch_list(coarse_chain_list_kernel, list, n, nx_max, gws, s);
 }
 
+__global__ void __launch_bounds__(256) row_sums_kernel(const double* x, int nx, double* out) {
+  __shared__ double red[8];
+  const double* row = x + (size_t)blockIdx.x * nx;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nx; i += 256) v += row[i];
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_row_sums(const double* x, int rows, int nx, double* out, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  row_sums_kernel<<<rows, 256, 0, s>>>(x, nx, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_correct(const CorrectArgs& c, double* gws, cudaStream_t s, bool cluster) {
   if (cluster && c.k < c.n_slices && coarse_cluster_ok(c.m)) return launch_correct_cluster(c, s);
   return launch_macro(correct_kernel, 1, c.m.nx, gws, s, c);

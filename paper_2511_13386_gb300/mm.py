@@ -88,7 +88,8 @@ class mm_parareal_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("err", ctypes.c_double * 64),
                 ("mass_drift", ctypes.c_double), ("fine_steps", ctypes.c_int64),
                 ("kinetic_updates", ctypes.c_int64), ("elapsed_ms", ctypes.c_double),
-                ("fine_ms", ctypes.c_double), ("fine_launches", ctypes.c_int32)]
+                ("fine_ms", ctypes.c_double), ("fine_launches", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32)]
 
 
 class mm_server_cfg(ctypes.Structure):
@@ -378,7 +379,8 @@ def parareal_run(ctx: Ctx, t_end: float, n_slices: int, max_iter: int, tol: floa
     return {"iterations": it, "err": [st.err[k] for k in range(min(it, 64))],
             "mass_drift": st.mass_drift, "fine_steps": st.fine_steps,
             "kinetic_updates": st.kinetic_updates, "elapsed_ms": st.elapsed_ms,
-            "fine_ms": st.fine_ms, "fine_launches": st.fine_launches}
+            "fine_ms": st.fine_ms, "fine_launches": st.fine_launches,
+            "kernel_launches": st.kernel_launches}
 
 
 def mm_coarse_guess(ctx: Ctx, n_slices: int, t_span: float, rho_slices, g_prev, stream=None):
@@ -397,7 +399,8 @@ def _stats_dict(st: "mm_parareal_stats") -> dict:
     return {"iterations": it, "err": [st.err[k] for k in range(min(it, 64))],
             "mass_drift": st.mass_drift, "fine_steps": st.fine_steps,
             "kinetic_updates": st.kinetic_updates, "elapsed_ms": st.elapsed_ms,
-            "fine_ms": st.fine_ms, "fine_launches": st.fine_launches}
+            "fine_ms": st.fine_ms, "fine_launches": st.fine_launches,
+            "kernel_launches": st.kernel_launches}
 
 
 class Batch:
