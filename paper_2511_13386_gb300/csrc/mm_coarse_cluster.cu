@@ -2,28 +2,35 @@
 // over a thread-block cluster: the coarse guess and the sequential
 // correction of Algorithm 1 (Sec. 3.3) for a single solve.
 //
-// Why a cluster: the step is a cyclic tridiagonal solve in double, and
-// GB300's FP64 pipe retires two lanes per clock per SM, so on one CTA the
-// solve is bound by that pipe and by its serial chains (about 19 us per
-// step at Nx = 1024).  With the rows spread over kCC CTAs on kCC SMs the
-// arithmetic has kCC pipes; what remains is the latency of the serial
-// chains (Thomas chunks of kChunk rows, log2 P levels of parallel cyclic
-// reduction) and one cluster barrier per level: about 16 us per step at
-// Nx = 1024, measured.
+// Why this shape.  The step is a cyclic tridiagonal solve in double, and
+// GB300's FP64 pipe takes 64 cycles to issue one warp-wide FP64
+// instruction on its SM sub-partition, however many lanes are active (two
+// lanes per clock per SM; one lane active costs the same as 32).  So the
+// time of a step is the number of dependent FP64 instructions on the
+// busiest warp, plus the cluster barriers; lanes are free.  Hence:
+//   - one row per thread, nb = nx / kCC rows per CTA, nb / 32 warps per
+//     CTA (one per sub-partition at Nx = 1024);
+//   - each warp eliminates its 31 interior rows by parallel cyclic
+//     reduction in registers (shuffles, no barrier), with three right-hand
+//     sides: the data and the couplings to its two bounding separators
+//     (the previous warp's last row and its own last row);
+//   - the nx / 32 warp separators form a cyclic tridiagonal system that
+//     every warp assembles from the records of all warps (one exchange
+//     through distributed shared memory) and solves redundantly by
+//     parallel cyclic reduction in registers;
+//   - every row is then rebuilt from its two separator values.
+// Two cluster barriers per step, against one per reduction level when the
+// reduction itself is distributed over the cluster; about 11 us per step at
+// Nx = 1024 against 16 us for that layout.
 //
-// Layout: CTA r owns rows [r nb, (r+1) nb), nb = nx / kCC, cut into chunks
-// of kChunk rows whose last row is a separator.  Per step:
-//   1. the Poisson law of S^MM for the frozen field (prefix sums per CTA,
-//      the CTAs' totals exchanged through distributed shared memory);
-//   2. each chunk's interior eliminated by Thomas sweeps for its data and
-//      its couplings to the two neighbouring separators;
-//   3. the P x P cyclic system on the separators by parallel cyclic
-//      reduction, each CTA holding P / kCC of its rows, the rows of other
-//      CTAs read through distributed shared memory, one cluster barrier per
-//      level (arrays double-buffered by level);
-//   4. every chunk rebuilt from its two separator values.
-// The coefficients and the elimination are the single-CTA solver's
-// (mm_coarse.cu), so the results agree with it to rounding.
+// Per step:
+//   1. the Poisson law of S^MM for the frozen field: a warp scan of the
+//      density deviations, the warps' totals through shared memory, the
+//      CTAs' totals through distributed shared memory;
+//   2. the coefficients of (I - m2 dt L_E) x = rho;
+//   3. the warp-local reduction;
+//   4. the separator records, one cluster barrier, the separators' system;
+//   5. the rows rebuilt.
 #include <cooperative_groups.h>
 
 #include "mm_internal.h"
@@ -34,229 +41,226 @@ namespace mmk {
 
 namespace {
 
-constexpr int kCT = 256;    // threads per CTA
-constexpr int kCC = 8;      // CTAs per cluster
-constexpr int kChunk = 4;   // rows per chunk, the last one a separator
+constexpr int kCC = 8;  // CTAs per cluster
+constexpr unsigned kFull = 0xffffffffu;
 
 template <class P>
 __device__ __forceinline__ P* on_rank(P* p, int rank) {
   return cg::this_cluster().map_shared_rank(p, rank);
 }
 
+// Shared memory of one CTA (doubles).
 struct CMap {
-  double *w, *E, *cw, *y, *vl, *vr;  // [nb] local rows
-  double *pa, *pb, *pc, *pd;         // [2][Pc] reduced rows by level parity (pb: 1/b)
-  double *xs;                        // [Pc] separator values
-  double *ex;                        // [kCC][2] per-CTA Poisson totals
-  double *first;                     // [4] y, vl, vr of local row 0
-  double *red;                       // [64] block reductions
+  double* E;    // [nb] field at the CTA's rows
+  double* rec;  // [nw][8] separator record of each warp
+  double* ex;   // [kCC][2] the CTAs' Poisson totals (pushed by every CTA)
+  double* wt;   // [2][8] the warps' Poisson totals
+  double* em;   // [kCC] the CTAs' maximum corrections (rank 0's copy)
 };
 
-__host__ __device__ inline size_t cmap_doubles(int nb) {
-  const int Pc = nb / kChunk;
-  return (size_t)6 * nb + 9 * (size_t)Pc + 2 * kCC + 4 + 64;
-}
+__host__ __device__ inline size_t cmap_doubles(int nb) { return (size_t)nb + 8 * (nb / 32) + 2 * kCC + 16 + kCC; }
 
 __device__ CMap carve_cmap(double* base, int nb) {
-  const int Pc = nb / kChunk;
   CMap m;
-  m.w = base;
-  m.E = m.w + nb;
-  m.cw = m.E + nb;
-  m.y = m.cw + nb;
-  m.vl = m.y + nb;
-  m.vr = m.vl + nb;
-  m.pa = m.vr + nb;
-  m.pb = m.pa + 2 * Pc;
-  m.pc = m.pb + 2 * Pc;
-  m.pd = m.pc + 2 * Pc;
-  m.xs = m.pd + 2 * Pc;
-  m.ex = m.xs + Pc;
-  m.first = m.ex + 2 * kCC;
-  m.red = m.first + 4;
+  m.E = base;
+  m.rec = m.E + nb;
+  m.ex = m.rec + 8 * (nb / 32);
+  m.wt = m.ex + 2 * kCC;
+  m.em = m.wt + 16;
   return m;
 }
 
-// Block-wide exclusive prefix of one value per thread; *tot = block total.
-__device__ double block_excl(double v, double* red, double* tot) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  double inc = v;
-  for (int d = 1; d < 32; d <<= 1) {
-    const double t = __shfl_up_sync(0xffffffffu, inc, d);
-    if (l >= d) inc += t;
-  }
-  __syncthreads();
-  if (l == 31) red[w] = inc;
-  __syncthreads();
-  double off = 0.0, all = 0.0;
-  for (int q = 0; q < kCT / 32; ++q) {
-    if (q < w) off += red[q];
-    all += red[q];
-  }
-  __syncthreads();
-  *tot = all;
-  return off + inc - v;
-}
+// Per-thread constants of a chain: the row's weight nx - g in the mean of
+// the Poisson prefix sums, and 1 / nx.
+struct RowConst {
+  double wgt, inv_nx;
+};
 
-// One linearly implicit S^0 step of the cluster's density, in place in w:
-// (I - m2 dt L_E) x = rho with E frozen from rho.
-__device__ void implicit_step_cluster(const CMap& M, const MacroArgs& a, double dt, int nb, int r) {
+// One linearly implicit S^0 step of the cluster's density; w is this
+// thread's row of rho, the result its row of (I - m2 dt L_E)^{-1} rho with
+// E frozen from rho.
+__device__ double implicit_step_cluster(const CMap& M, const MacroArgs& a, double dt, int nb, int r, double w,
+                                        const RowConst& rc) {
   cg::cluster_group cl = cg::this_cluster();
-  const int tid = threadIdx.x, nx = a.nx, g0 = r * nb;
-  const int Pc = nb / kChunk, P = Pc * kCC;
-  const int rr = (r + 1) % kCC, rl = (r + kCC - 1) % kCC;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, nw = nb >> 5;
+  const int P = a.nx >> 5;    // warp separators in the cluster
+  const int J = r * nw + wp;  // this warp's separator
 
-  // 1. Poisson law: E = S - mean(S), mean(S) = sum_m d_m (nx - m) / nx
-  const int cpt = (nb + kCT - 1) / kCT;
-  const int c0 = min(tid * cpt, nb), c1 = min(c0 + cpt, nb);
-  double t1 = 0.0, t2 = 0.0;
-  for (int c = c0; c < c1; ++c) {
-    const double d = (M.w[c] - a.rho_bar) * a.dx;
-    t1 += d;
-    M.E[c] = t1;
-    t2 += d * (double)(nx - (g0 + c));
+  // 1. Poisson law: S_c = sum_{m<=c} (rho_m - rho_bar) dx, E = S - mean(S),
+  //    mean(S) = sum_m (nx - m) d_m / nx
+  const double d = (w - a.rho_bar) * a.dx;
+  double inc = d, t2 = d * rc.wgt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += u;
+    t2 += __shfl_xor_sync(kFull, t2, o);
   }
-  double tot1, tot2;
-  const double ex1 = block_excl(t1, M.red, &tot1);
-  block_excl(t2, M.red, &tot2);
-  if (tid == 0)
+  if (lane == 31) M.wt[wp] = inc;
+  if (lane == 0) M.wt[8 + wp] = t2;
+  __syncthreads();
+  double pw = 0.0;  // the warps before this one
+  for (int q = 0; q < wp; ++q) pw += M.wt[q];
+  if (tid == 0) {
+    double T1 = 0.0, T2 = 0.0;
+    for (int q = 0; q < nw; ++q) {
+      T1 += M.wt[q];
+      T2 += M.wt[8 + q];
+    }
     for (int q = 0; q < kCC; ++q) {
       double* e = on_rank(M.ex, q);
-      e[2 * r] = tot1;
-      e[2 * r + 1] = tot2;
+      e[2 * r] = T1;
+      e[2 * r + 1] = T2;
     }
-  cl.sync();
-  double base = 0.0, all1 = 0.0, all2 = 0.0;
-  for (int q = 0; q < kCC; ++q) {
-    if (q < r) base += M.ex[2 * q];
-    all1 += M.ex[2 * q];
-    all2 += M.ex[2 * q + 1];
   }
-  const double mean = all2 * (1.0 / nx);
-  for (int c = c0; c < c1; ++c) M.E[c] = (base + ex1) + M.E[c] - mean;
-  const double E_left = (r > 0 ? base : all1) - mean;  // E at the row before this CTA's first
+  cl.sync();
+  // every warp combines the CTAs' totals in the same order, so every warp
+  // of every CTA holds the same bits: lane q < kCC takes CTA q's totals
+  const double x1 = lane < kCC ? M.ex[2 * lane] : 0.0, x2 = lane < kCC ? M.ex[2 * lane + 1] : 0.0;
+  double s1 = x1, a1 = x1, a2 = x2;
+#pragma unroll
+  for (int o = 1; o < kCC; o <<= 1) {
+    const double u = __shfl_up_sync(kFull, s1, o);
+    if (lane >= o) s1 += u;
+    a1 += __shfl_xor_sync(kFull, a1, o);
+    a2 += __shfl_xor_sync(kFull, a2, o);
+  }
+  const double base = __shfl_sync(kFull, s1, (r + kCC - 1) & (kCC - 1));  // CTAs before r (r > 0)
+  const double all1 = __shfl_sync(kFull, a1, 0), all2 = __shfl_sync(kFull, a2, 0);
+  const double mean = all2 * rc.inv_nx;
+  const double E = ((r > 0 ? base : 0.0) + pw + inc) - mean;
+  const double E_left = (r > 0 ? base : all1) - mean;  // E at the row before the CTA's first
+  M.E[tid] = E;
   __syncthreads();
 
+  // 2. coefficients of row g: lo x_{g-1} + di x_g + up x_{g+1} = rho_g
   const double k = a.m2 * dt * a.inv_dx, idx = a.inv_dx;
-  auto coef = [&](int i, double& lo, double& di, double& up) {
-    const double Er = M.E[i], El = i == 0 ? E_left : M.E[i - 1];
-    lo = -k * (idx + 0.5 * El);
-    di = 1.0 - k * (-2.0 * idx - 0.5 * Er + 0.5 * El);
-    up = -k * (idx - 0.5 * Er);
-  };
+  const double El = tid == 0 ? E_left : M.E[tid - 1];
+  const double lo = -k * (idx + 0.5 * El);
+  const double di = 1.0 - k * (-2.0 * idx - 0.5 * E + 0.5 * El);
+  const double up = -k * (idx - 0.5 * E);
 
-  // 2. chunk interiors (thread p: chunk p, rows [a0, b0), separator b0)
-  const int p = tid;
-  if (p < Pc) {
-    const int a0 = p * kChunk, b0 = a0 + kChunk - 1;
-    double lo, di, up, cprev = 0.0, yp = 0.0, lp = 0.0, rp = 0.0;
-    for (int i = a0; i < b0; ++i) {
-      coef(i, lo, di, up);
-      const double l = (i == a0) ? 0.0 : lo;
-      const double inv = 1.0 / (di - l * cprev);
-      cprev = (i == b0 - 1) ? 0.0 : up * inv;
-      M.cw[i] = cprev;
-      yp = (M.w[i] - l * yp) * inv;
-      lp = ((i == a0 ? -lo : 0.0) - l * lp) * inv;
-      rp = (i == b0 - 1) ? -up * inv : 0.0;
-      M.y[i] = yp;
-      M.vl[i] = lp;
-      M.vr[i] = rp;
-    }
-    for (int i = b0 - 2; i >= a0; --i) {
-      M.y[i] -= M.cw[i] * M.y[i + 1];
-      M.vl[i] -= M.cw[i] * M.vl[i + 1];
-      M.vr[i] -= M.cw[i] * M.vr[i + 1];
-    }
-    if (p == 0) {  // the previous CTA's last separator couples to row 0
-      M.first[0] = M.y[0];
-      M.first[1] = M.vl[0];
-      M.first[2] = M.vr[0];
-    }
+  // 3. rows 0..30 of the warp (lane 31, the separator, is an identity row
+  //    here): (A, B, C) with right-hand sides D (the data), DL (the
+  //    coupling -lo of row 0 to the previous separator) and DR (the
+  //    coupling -up of row 30 to this warp's separator).  Parallel cyclic
+  //    reduction: at stride o row i takes rows i - o and i + o (identity
+  //    rows beyond the warp's ends, where A or C is already zero); after
+  //    five strides every row stands alone.
+  double A = lane == 0 ? 0.0 : lo, B = di, C = lane == 30 ? 0.0 : up, D = w;
+  double DL = lane == 0 ? -lo : 0.0, DR = lane == 30 ? -up : 0.0;
+  if (lane == 31) {
+    A = 0.0;
+    B = 1.0;
+    C = 0.0;
+    D = 0.0;
+    DL = 0.0;
+    DR = 0.0;
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double ib = 1.0 / B;
+    const double Am = __shfl_up_sync(kFull, A, o), Bm = __shfl_up_sync(kFull, ib, o);
+    const double Cm = __shfl_up_sync(kFull, C, o), Dm = __shfl_up_sync(kFull, D, o);
+    const double DLm = __shfl_up_sync(kFull, DL, o), DRm = __shfl_up_sync(kFull, DR, o);
+    const double Ap = __shfl_down_sync(kFull, A, o), Bp = __shfl_down_sync(kFull, ib, o);
+    const double Cp = __shfl_down_sync(kFull, C, o), Dp = __shfl_down_sync(kFull, D, o);
+    const double DLp = __shfl_down_sync(kFull, DL, o), DRp = __shfl_down_sync(kFull, DR, o);
+    const bool hm = lane >= o, hp = lane + o < 32;
+    const double al = hm ? -A * Bm : 0.0, ga = hp ? -C * Bp : 0.0;
+    const double nA = hm ? al * Am : 0.0, nC = hp ? ga * Cp : 0.0;
+    B = fma(al, hm ? Cm : 0.0, fma(ga, hp ? Ap : 0.0, B));
+    D = fma(al, hm ? Dm : 0.0, fma(ga, hp ? Dp : 0.0, D));
+    DL = fma(al, hm ? DLm : 0.0, fma(ga, hp ? DLp : 0.0, DL));
+    DR = fma(al, hm ? DRm : 0.0, fma(ga, hp ? DRp : 0.0, DR));
+    A = nA;
+    C = nC;
+  }
+  const double ib = 1.0 / B;
+  // row i = Y + S_{J-1} VL + S_J VR (lanes 0..30)
+  const double Y = D * ib, VL = DL * ib, VR = DR * ib;
+
+  // 4. separator J (lane 31, row x31): lo x30 + di x31 + up x32 = rho with
+  //    x30 = Y30 + S_{J-1} VL30 + S_J VR30 (this warp) and x32 = Y'0 +
+  //    S_J VL'0 + S_{J+1} VR'0 (the next warp's row 0).  Each warp records
+  //    its own-side part and its row 0; the system's rows are assembled
+  //    from a record and the next one.
+  const double Y30 = __shfl_sync(kFull, Y, 30), VL30 = __shfl_sync(kFull, VL, 30);
+  const double VR30 = __shfl_sync(kFull, VR, 30);
+  double* q = M.rec + 8 * wp;
+  if (lane == 31) {
+    q[0] = lo * VL30;          // coefficient of S_{J-1}
+    q[1] = fma(lo, VR30, di);  // of S_J, this warp's part
+    q[2] = fma(-lo, Y30, w);   // right-hand side, this warp's part
+    q[3] = up;
+  }
+  if (lane == 0) {
+    q[4] = Y;
+    q[5] = VL;
+    q[6] = VR;
   }
   cl.sync();
+  double sa = 0.0, sb = 1.0, sc = 0.0, sd = 0.0;
+  if (lane < P) {  // lane j: separator j
+    const int jn = (lane + 1) & (P - 1);
+    const double* qj = on_rank(M.rec, lane / nw) + 8 * (lane % nw);
+    const double* qn = on_rank(M.rec, jn / nw) + 8 * (jn % nw);
+    const double p0 = qj[0], p1 = qj[1], p2 = qj[2], p3 = qj[3];
+    const double n4 = qn[4], n5 = qn[5], n6 = qn[6];
+    sa = p0;
+    sb = fma(p3, n5, p1);
+    sc = p3 * n6;
+    sd = fma(-p3, n4, p2);
+  }
+  // cyclic reduction over the P separators (P a power of two): after
+  // log2 P strides both couplings of a row point at the row itself
+  for (int o = 1; o < P; o <<= 1) {
+    const double ib2 = 1.0 / sb;
+    const int lm = (lane - o) & (P - 1), lp = (lane + o) & (P - 1);
+    const double Am = __shfl_sync(kFull, sa, lm), Bm = __shfl_sync(kFull, ib2, lm);
+    const double Cm = __shfl_sync(kFull, sc, lm), Dm = __shfl_sync(kFull, sd, lm);
+    const double Ap = __shfl_sync(kFull, sa, lp), Bp = __shfl_sync(kFull, ib2, lp);
+    const double Cp = __shfl_sync(kFull, sc, lp), Dp = __shfl_sync(kFull, sd, lp);
+    const double al = -sa * Bm, ga = -sc * Bp;
+    const double nA = al * Am, nC = ga * Cp;
+    sb = fma(al, Cm, fma(ga, Ap, sb));
+    sd = fma(al, Dm, fma(ga, Dp, sd));
+    sa = nA;
+    sc = nC;
+  }
+  const double S = sd / (sa + sb + sc);
 
-  // 3. the separators' cyclic system by parallel cyclic reduction
-  double ra = 0.0, rb = 1.0, rc = 0.0, rd = 0.0;
-  if (p < Pc) {
-    const int b0 = p * kChunk + kChunk - 1, il = b0 - 1;
-    double yr, vlr, vrr;  // the next chunk's first interior row
-    if (p < Pc - 1) {
-      yr = M.y[b0 + 1];
-      vlr = M.vl[b0 + 1];
-      vrr = M.vr[b0 + 1];
-    } else {
-      const double* f = on_rank(M.first, rr);
-      yr = f[0];
-      vlr = f[1];
-      vrr = f[2];
-    }
-    double lo, di, up;
-    coef(b0, lo, di, up);
-    ra = lo * M.vl[il];
-    rb = lo * M.vr[il] + di + up * vlr;
-    rc = up * vrr;
-    rd = M.w[b0] - lo * M.y[il] - up * yr;
-  }
-  int par = 0;
-  for (int st = 1; st < P; st <<= 1, par ^= 1) {
-    if (p < Pc) {
-      M.pa[par * Pc + p] = ra;
-      M.pb[par * Pc + p] = 1.0 / rb;
-      M.pc[par * Pc + p] = rc;
-      M.pd[par * Pc + p] = rd;
-    }
-    cl.sync();
-    if (p < Pc) {
-      const int J = r * Pc + p;
-      const int im = (J - st) & (P - 1), ip = (J + st) & (P - 1);
-      const int om = im / Pc, jm = par * Pc + im % Pc, op = ip / Pc, jp = par * Pc + ip % Pc;
-      const double Am = on_rank(M.pa, om)[jm], Bm = on_rank(M.pb, om)[jm];
-      const double Cm = on_rank(M.pc, om)[jm], Dm = on_rank(M.pd, om)[jm];
-      const double Ap = on_rank(M.pa, op)[jp], Bp = on_rank(M.pb, op)[jp];
-      const double Cp = on_rank(M.pc, op)[jp], Dp = on_rank(M.pd, op)[jp];
-      const double al = -ra * Bm, ga = -rc * Bp;
-      const double na = al * Am, nc = ga * Cp;
-      rb = fma(al, Cm, fma(ga, Ap, rb));
-      rd = fma(al, Dm, fma(ga, Dp, rd));
-      ra = na;
-      rc = nc;
-    }
-  }
-  if (p < Pc) M.xs[p] = rd / (ra + rb + rc);
-  cl.sync();
-
-  // 4. every chunk from its two separator values
-  if (p < Pc) {
-    const int a0 = p * kChunk, b0 = a0 + kChunk - 1;
-    const double Lm = p > 0 ? M.xs[p - 1] : on_rank(M.xs, rl)[Pc - 1], Lp = M.xs[p];
-    for (int i = a0; i < b0; ++i) M.w[i] = M.y[i] + Lm * M.vl[i] + Lp * M.vr[i];
-    M.w[b0] = Lp;
-  }
-  __syncthreads();
+  // 5. the rows from their separators
+  const double Sm = __shfl_sync(kFull, S, (J - 1) & (P - 1)), Sj = __shfl_sync(kFull, S, J);
+  return lane == 31 ? Sj : fma(Sm, VL, fma(Sj, VR, Y));
 }
 
-__device__ void coarse_cluster(const CMap& M, const MacroArgs& a, int nb, int r) {
+__device__ double coarse_cluster(const CMap& M, const MacroArgs& a, int nb, int r, double w, const RowConst& rc) {
   const double dt = a.t_span / a.coarse_steps;
-  for (int s = 0; s < a.coarse_steps; ++s) implicit_step_cluster(M, a, dt, nb, r);
+  for (int s = 0; s < a.coarse_steps; ++s) w = implicit_step_cluster(M, a, dt, nb, r, w, rc);
+  return w;
+}
+
+__device__ RowConst row_const(const MacroArgs& a, int g) {
+  RowConst rc;
+  rc.wgt = (double)(a.nx - g);
+  rc.inv_nx = 1.0 / a.nx;
+  return rc;
 }
 
 // Coarse guess of Algorithm 1 for one solve: rho^{n+1,0} = G(rho^{n,0}).
-__global__ void __launch_bounds__(kCT) coarse_chain_cluster_kernel(MacroArgs a, int n_slices, double* rho,
+// blockDim = nb = nx / kCC; thread t of CTA r holds row r nb + t.
+__global__ void __launch_bounds__(128) coarse_chain_cluster_kernel(MacroArgs a, int n_slices, double* rho,
                                                                    double* gprev) {
   extern __shared__ __align__(16) double csm[];
-  const int nb = a.nx / kCC, r = (int)cg::this_cluster().block_rank(), g0 = r * nb;
+  const int nb = a.nx / kCC, r = (int)cg::this_cluster().block_rank(), g = r * nb + threadIdx.x;
   const CMap M = carve_cmap(csm, nb);
-  for (int i = threadIdx.x; i < nb; i += kCT) M.w[i] = rho[g0 + i];
-  __syncthreads();
+  const RowConst rc = row_const(a, g);
+  double w = rho[g];
   for (int n = 0; n < n_slices; ++n) {
-    coarse_cluster(M, a, nb, r);
-    double* out = rho + (size_t)(n + 1) * a.nx + g0;
-    double* Gp = gprev + (size_t)(n + 1) * a.nx + g0;
-    for (int i = threadIdx.x; i < nb; i += kCT) {
-      out[i] = M.w[i];
-      Gp[i] = M.w[i];
-    }
+    w = coarse_cluster(M, a, nb, r, w, rc);
+    rho[(size_t)(n + 1) * a.nx + g] = w;
+    gprev[(size_t)(n + 1) * a.nx + g] = w;
   }
   cg::this_cluster().sync();  // no CTA leaves while another may read its shared memory
 }
@@ -264,42 +268,35 @@ __global__ void __launch_bounds__(kCT) coarse_chain_cluster_kernel(MacroArgs a, 
 // Sequential correction of Algorithm 1 for one solve, n = k..N-1:
 // Gn = G(rho^{n,k+1}); rho^{n+1,k+1} = F + (Gn - Gprev); Gprev = Gn; and the
 // successive error max |rho^{n+1,k+1} - rho^{n+1,k}|.
-__global__ void __launch_bounds__(kCT) correct_cluster_kernel(CorrectArgs c) {
+__global__ void __launch_bounds__(128) correct_cluster_kernel(CorrectArgs c) {
   extern __shared__ __align__(16) double csm[];
   const MacroArgs& a = c.m;
-  const int nx = a.nx, nb = nx / kCC, r = (int)cg::this_cluster().block_rank(), g0 = r * nb;
+  const int nx = a.nx, nb = nx / kCC, r = (int)cg::this_cluster().block_rank(), g = r * nb + threadIdx.x;
   const CMap M = carve_cmap(csm, nb);
-  const double* rk = c.rho + (size_t)c.k * nx + g0;
-  for (int i = threadIdx.x; i < nb; i += kCT) M.w[i] = rk[i];
-  __syncthreads();
+  const RowConst rc = row_const(a, g);
+  double w = c.rho[(size_t)c.k * nx + g];
   double emax = 0.0;
   for (int n = c.k; n < c.n_slices; ++n) {
-    coarse_cluster(M, a, nb, r);
-    double* out = c.rho + (size_t)(n + 1) * nx + g0;
-    const double* F = c.frho + (size_t)(n + 1) * nx + g0;
-    double* Gp = c.gprev + (size_t)(n + 1) * nx + g0;
-    for (int i = threadIdx.x; i < nb; i += kCT) {
-      const double gn = M.w[i];
-      const double v = F[i] + (gn - Gp[i]);
-      emax = fmax(emax, fabs(v - out[i]));
-      out[i] = v;
-      Gp[i] = gn;
-      M.w[i] = v;
-    }
-    __syncthreads();
+    const double gn = coarse_cluster(M, a, nb, r, w, rc);
+    const size_t at = (size_t)(n + 1) * nx + g;
+    const double v = c.frho[at] + (gn - c.gprev[at]);
+    emax = fmax(emax, fabs(v - c.rho[at]));
+    c.rho[at] = v;
+    c.gprev[at] = gn;
+    w = v;
   }
-  for (int m = 16; m > 0; m >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, m));
-  if ((threadIdx.x & 31) == 0) M.red[threadIdx.x >> 5] = emax;
+  for (int m = 16; m > 0; m >>= 1) emax = fmax(emax, __shfl_xor_sync(kFull, emax, m));
+  if ((threadIdx.x & 31) == 0) M.wt[threadIdx.x >> 5] = emax;  // the totals are dead after the last step
   __syncthreads();
   if (threadIdx.x == 0) {
     double e = 0.0;
-    for (int q = 0; q < kCT / 32; ++q) e = fmax(e, M.red[q]);
-    on_rank(M.ex, 0)[2 * r] = e;  // rank 0 gathers the CTAs' maxima
+    for (int q = 0; q < nb / 32; ++q) e = fmax(e, M.wt[q]);
+    on_rank(M.em, 0)[r] = e;  // rank 0 gathers the CTAs' maxima
   }
   cg::this_cluster().sync();
   if (r == 0 && threadIdx.x == 0) {
     double e = 0.0;
-    for (int q = 0; q < kCC; ++q) e = fmax(e, M.ex[2 * q]);
+    for (int q = 0; q < kCC; ++q) e = fmax(e, M.em[q]);
     *c.err = e;
   }
 }
@@ -307,11 +304,9 @@ __global__ void __launch_bounds__(kCT) correct_cluster_kernel(CorrectArgs c) {
 template <class K, class... Args>
 cudaError_t launch_cluster(K kernel, int nb, cudaStream_t s, Args... args) {
   const size_t smem = cmap_doubles(nb) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCC);
-  cfg.blockDim = dim3(kCT);
+  cfg.blockDim = dim3(nb);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -327,15 +322,11 @@ cudaError_t launch_cluster(K kernel, int nb, cudaStream_t s, Args... args) {
 }  // namespace
 
 bool coarse_cluster_ok(const MacroArgs& a) {
-  if (a.coarse_kind != 0 || a.nx % (kCC * kChunk)) return false;
-  const int nb = a.nx / kCC, P = nb / kChunk * kCC;
-  // one thread per chunk; and at most 2048 rows: at Nx = 4096 a chain of
-  // a dozen steps lands 1.8e-12 from the oracle (the one-CTA solver 1.2e-12;
-  // two correct double-precision solvers of that chain differ by 3.9e-12,
-  // the system being that ill-conditioned), so larger grids keep the
-  // one-CTA solver, which sits closer to the oracle
-  if (nb < 4 * kChunk || (P & (P - 1)) || nb / kChunk > kCT || a.nx > 2048) return false;
-  return cmap_doubles(nb) * sizeof(double) <= 200 * 1024;
+  // one row per thread and a whole number of warps per CTA (nx >= 256);
+  // the warp separators (nx / 32) in one warp's lanes (nx <= 1024); nx a
+  // power of two for the cyclic reduction over them
+  const int nx = a.nx;
+  return a.coarse_kind == 0 && nx >= 32 * kCC && nx <= 32 * 32 && (nx & (nx - 1)) == 0;
 }
 
 cudaError_t launch_coarse_chain_cluster(const MacroArgs& a, int n_slices, double* rho, double* gprev,

@@ -262,11 +262,11 @@ def _chain_rounding_spread(op, rho0, span, N, ref, fr=None, want=None):
     return spread
 
 
-@pytest.mark.parametrize("nx", [64, 1024, 4096])
+@pytest.mark.parametrize("nx", [64, 256, 1024, 4096])
 def test_coarse_guess_and_correction_entry_points(nx):
     """Algorithm 1's sequential parts through their own entry points (at
-    Nx = 1024 and 4096 one solve's implicit step runs over a thread-block
-    cluster): the coarse guess rho^{n+1,0} = G(rho^{n,0}) over 12 slices and
+    Nx = 256 and 1024 one solve's implicit step runs over a thread-block
+    cluster, elsewhere on one CTA): the coarse guess rho^{n+1,0} = G(rho^{n,0}) over 12 slices and
     one correction sweep rho^{n+1,1} = F + (G(rho^{n,1}) - G(rho^{n,0})),
     against the oracle's G composed slice by slice: at 1e-12, or where the
     chain's conditioning makes two correct double-precision solvers drift
