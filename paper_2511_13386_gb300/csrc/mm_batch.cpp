@@ -171,6 +171,46 @@ extern "C" mm_status mm_batch_add(mm_batch* b, const mm_params* p, const mm_para
 }
 
 // One parareal iteration of every unfinished solve.
+// Grids from which a solve's sequential parts (coarse guess, correction)
+// run over a thread-block cluster, one cluster of 8 SMs per solve, instead
+// of one CTA: there the one-CTA step is bound by its SM's FP64 pipe (0.7 ms
+// per step at Nx = 32768).  Below them a batch's many solves keep every
+// SM's FP64 pipe busy with one CTA each, which does less work per step in
+// total than the cluster layout.
+constexpr int kClusterMinNx = 16384;
+
+static bool on_cluster(const mmk::CorrectArgs& c) { return c.m.nx >= kClusterMinNx && mmk::coarse_cluster_ok(c.m); }
+
+// Orders `ca` for launch_sequential: the one-CTA entries first, then the
+// cluster entries grouped by grid size; returns the one-CTA count.
+static int order_sequential(std::vector<mmk::CorrectArgs>& ca) {
+  std::stable_sort(ca.begin(), ca.end(), [](const mmk::CorrectArgs& x, const mmk::CorrectArgs& y) {
+    return (on_cluster(x) ? x.m.nx : 0) < (on_cluster(y) ? y.m.nx : 0);
+  });
+  int n = 0;
+  while (n < (int)ca.size() && !on_cluster(ca[n])) ++n;
+  return n;
+}
+
+// The coarse guesses (guess = true) or the corrections of the entries of
+// `ca`, ordered by order_sequential and uploaded to d: one work-list launch
+// of one CTA per solve, then one cluster launch per grid size.
+static cudaError_t launch_sequential(const std::vector<mmk::CorrectArgs>& ca, const mmk::CorrectArgs* d,
+                                     int n_small, bool guess, int nx_max, double* ws, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (n_small > 0)
+    e = guess ? mmk::launch_coarse_chain_list(d, n_small, nx_max, ws, s)
+              : mmk::launch_correct_list(d, n_small, nx_max, ws, s);
+  for (int i = n_small; e == cudaSuccess && i < (int)ca.size();) {
+    int j = i;
+    while (j < (int)ca.size() && ca[j].m.nx == ca[i].m.nx) ++j;
+    e = guess ? mmk::launch_coarse_chain_cluster_list(d + i, j - i, ca[i].m.nx, s)
+              : mmk::launch_correct_cluster_list(d + i, j - i, ca[i].m.nx, s);
+    i = j;
+  }
+  return e;
+}
+
 extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* stream) {
   if (!b) return mm_fail(MM_ERR_INVALID, "batch is NULL");
   cudaSetDevice(b->device);
@@ -207,9 +247,9 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
       ca.push_back(c);
       v->started = true;
     }
+    const int n_small = order_sequential(ca);
     e = cudaMemcpyAsync(d_corr, ca.data(), sizeof(mmk::CorrectArgs) * ca.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = mmk::launch_coarse_chain_list(d_corr, (int)ca.size(), nx_max, (double*)b->macro_ws.p, s);
+    if (e == cudaSuccess) e = launch_sequential(ca, d_corr, n_small, true, nx_max, (double*)b->macro_ws.p, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "batch: coarse guess");
     // the argument table is reused below: the copy above must be consumed
     e = cudaStreamSynchronize(s);
@@ -313,8 +353,9 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
     c.err = d_err + q;
     ca.push_back(c);
   }
+  const int n_small = order_sequential(ca);
   e = cudaMemcpyAsync(d_corr, ca.data(), sizeof(mmk::CorrectArgs) * ca.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = mmk::launch_correct_list(d_corr, (int)ca.size(), nx_max, (double*)b->macro_ws.p, s);
+  if (e == cudaSuccess) e = launch_sequential(ca, d_corr, n_small, false, nx_max, (double*)b->macro_ws.p, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "batch: corrections");
   std::vector<double> errs(act.size());
   std::vector<unsigned long long> kin(act.size());

@@ -204,6 +204,10 @@ bool coarse_cluster_ok(const MacroArgs& a);
 cudaError_t launch_coarse_chain_cluster(const MacroArgs& a, int n_slices, double* rho, double* gprev,
                                         cudaStream_t s);
 cudaError_t launch_correct_cluster(const CorrectArgs& c, cudaStream_t s);
+// The same for n solves of one grid size nx (coarse_cluster_ok), one cluster
+// each; `list` in device memory.
+cudaError_t launch_coarse_chain_cluster_list(const CorrectArgs* list, int n, int nx, cudaStream_t s);
+cudaError_t launch_correct_cluster_list(const CorrectArgs* list, int n, int nx, cudaStream_t s);
 // out[r] = sum of row r of x ([rows][nx]): the slices' mass, which the
 // parareal driver reports as its mass drift.
 cudaError_t launch_row_sums(const double* x, int rows, int nx, double* out, cudaStream_t s);

@@ -210,3 +210,29 @@ def test_batch_extreme_many_solve_shapes_match_oracle(eps, shapes):
         assert info["iterations"] == it == 1
         assert rel(o, ref) <= FP32_TOL, (p.nx, p.nv, rel(o, ref))
         assert info["mass_drift"] <= 1e-12
+
+
+def test_batch_large_grid_sequential_parts_on_a_cluster():
+    """A solve of Nx = 16384 in the batch engine: its coarse guess and
+    corrections run over a thread-block cluster (chunks of 16 rows per
+    thread), as in parareal_run; the result matches the single-solve run,
+    and the oracle at 1e-12 or, where the implicit step's conditioning
+    (about 2.5e4 here) makes a correct double-precision evaluation drift
+    further, within twice the oracle's own change under one-ulp
+    perturbations of rho0."""
+    nx, nv, N, K = 16384, 16, 5, 2
+    w = W.batched(nx, nv, 1e-2, seed=W.SEED_BASE + 77, n_slices=N)
+    p = params(nx, nv, 1e-2, mm.MM_FP64, rho_bar=1.0)
+    ctx = mm.mm_create(p)
+    dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+    ctx.close()
+    t_end = N * 3 * dt * (1 - 1e-9)
+    outs, infos, _ = _run_batch([(p, w, t_end, N, K)])
+    single, sinfo = _single(p, w, t_end, N, K)
+    assert infos[0]["iterations"] == sinfo["iterations"] == K
+    assert rel(outs[0], single) <= FP64_TOL, rel(outs[0], single)
+    ref, _, it = O.parareal(oparams(p), w.rho0, w.g0, t_end, N, K)
+    assert it == K
+    bound = max(FP64_TOL, 2 * _sensitivity(p, w, t_end, N, K, ref))
+    assert rel(outs[0], ref) <= bound, (rel(outs[0], ref), bound)
+    assert infos[0]["mass_drift"] <= 1e-12
