@@ -70,6 +70,13 @@ def parse():
                          "states of Nx=4096, Nv=128 (HBM-streaming); many: 2048 independent solves of random "
                          "sizes in one batch; serving: open-loop Poisson arrivals through the server")
     ap.add_argument("--solves", type=int, default=2048, help="solves of the many-solve workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: keep the context's default launch shape of F instead of timing "
+                         "the candidates (profiler runs, whose timings would pick another shape)")
+    ap.add_argument("--chunk-entry", type=float, default=None,
+                    help="batched workload: the resident kernel's chunk entry cost in steps for the launch "
+                         "planner, instead of the autotuner's measurement (profiler runs, where every launch "
+                         "is slower, use the plain run's value to keep its launch plan)")
     ap.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals (serving)")
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second (serving)")
     a = ap.parse_args()
@@ -306,8 +313,11 @@ def run_ours(a, rank, world, dist):
     rho_b, g_b = w.with_batch(8)
     tr = torch.tensor(rho_b, device=dev).repeat(N_SLICES // 8, 1).contiguous()
     tg = torch.tensor(g_b, device=dev, dtype=gdt).repeat(N_SLICES // 8, 1, 1).contiguous()
-    tune = mm.mm_autotune(ctx, N_SLICES, 64, tr, tg, torch.empty_like(tr), torch.empty_like(tg))
+    tune = None if a.no_autotune else mm.mm_autotune(ctx, N_SLICES, 64, tr, tg, torch.empty_like(tr),
+                                                        torch.empty_like(tg))
     del tr, tg
+    if a.chunk_entry is not None:  # a fixed launch plan (e.g. under a profiler, which inflates the measurement)
+        mm.mm_set_chunk_entry(ctx, a.chunk_entry)
     q = mm.mm_query(ctx, T_END / N_SLICES)
     stream = torch.cuda.current_stream()
     rho0 = torch.tensor(w.rho0, device=dev)
@@ -398,10 +408,16 @@ def run_ours(a, rank, world, dist):
                 "hbm_equivalent": {"achieved_gbs": round(alg_gbs, 1), "peak_gbs": hbm_peak,
                                    "frac_of_measured": round(alg_gbs / hbm_peak, 3)}}
     ctx.close()
-    autotune = {"chosen": kname, "chunk_entry_steps_measured": round(tune["res_entry_steps"], 2),
-                "candidates_ms_64_steps": {
-        (f"resident cluster {c['cluster']}" if c["fine_kernel"] == 2 else f"streaming {c['vpt']} nodes/lane"):
-            round(c["ms"], 3) for c in tune["candidates"]}}
+    if tune is None:
+        autotune = {"chosen": kname, "skipped": "--no-autotune: the context's default launch shape",
+                    "chunk_entry_steps_used": a.chunk_entry}
+    else:
+        autotune = {"chosen": kname, "chunk_entry_steps_measured": round(tune["res_entry_steps"], 2),
+                    "chunk_entry_steps_used": a.chunk_entry if a.chunk_entry is not None
+                    else round(tune["res_entry_steps"], 2),
+                    "candidates_ms_64_steps": {
+            (f"resident cluster {c['cluster']}" if c["fine_kernel"] == 2 else f"streaming {c['vpt']} nodes/lane"):
+                round(c["ms"], 3) for c in tune["candidates"]}}
     return {"value": value, "total_ms": total_ms, "step_ms": step_ms, "wall": wall, "autotune": autotune,
             "updates_per_step": updates_per_step, "e2e": e2e, "roofline": roofline,
             "clocks": clk.summary(), "n_steps_fine": q["n_steps"], "fine_launches": fine_n,

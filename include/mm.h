@@ -286,6 +286,16 @@ MM_API mm_status mm_autotune(mm_ctx* ctx, int32_t batch, int32_t steps, const do
                              const void* g_in, double* rho_out, void* g_out, mm_tune_result* out,
                              void* stream);
 
+/* Sets the cost of a resident-kernel step chunk's entry and exit, in steps,
+   that the launch planner uses when a batch is larger than the GPU holds at
+   once (the quantity mm_autotune measures; a later mm_autotune overwrites
+   it).  For reproducing a launch plan under a tool that slows every launch
+   (a profiler), where the measurement would be inflated.  The results do
+   not depend on it: only the number of launches and their step counts.
+     entry_steps  >= 0, at most 1000; 0 selects the built-in estimate
+   Errors: MM_ERR_INVALID. */
+MM_API mm_status mm_set_chunk_entry(mm_ctx* ctx, double entry_steps);
+
 /* G over a span (Sec. 2.3, eq. S^0): coarse_steps linearly implicit steps
    (E frozen from the old density, cyclic tridiagonal solve) or explicit S^0
    steps, for every density of the batch.  rho_in and rho_out may alias.

@@ -1091,6 +1091,13 @@ extern "C" mm_status parareal_run(mm_ctx* c, const mm_parareal_cfg* cfg, const d
   return MM_OK;
 }
 
+extern "C" mm_status mm_set_chunk_entry(mm_ctx* c, double entry_steps) {
+  if (!c) return mm_fail(MM_ERR_INVALID, "ctx is NULL");
+  if (!(entry_steps >= 0.0 && entry_steps <= 1000.0)) return mm_fail(MM_ERR_INVALID, "entry_steps outside [0, 1000]");
+  c->res_entry = entry_steps;
+  return MM_OK;
+}
+
 // --------------------------------------------- fine plan without buffers --
 
 // Kernel arguments of F for one call, with every buffer pointer left unset

@@ -29,7 +29,7 @@
 //
 // Precision (FP32-g path): g, the sweep and the per-lane partial moments in
 // float; the density in float-float; the Poisson prefix sum in float-float;
-// the per-interface moment combination by compensated (two-sum) summation;
+// the per-interface moments as float sums of the lane partials;
 // one float flux per interface, added to one cell and subtracted from the
 // other, so mass is conserved to float-float rounding.
 #include <math.h>
@@ -55,7 +55,6 @@ struct MP;
 template <>
 struct MP<double> {
   using R = double;   // density / Poisson arithmetic
-  using A = double;   // moment accumulator
   static __device__ __forceinline__ R c(double x) { return x; }
   static __device__ __forceinline__ R add(R a, R b) { return a + b; }
   static __device__ __forceinline__ R sub(R a, R b) { return a - b; }
@@ -67,10 +66,6 @@ struct MP<double> {
   static __device__ __forceinline__ R zero() { return 0.0; }
   static __device__ __forceinline__ R shfl_up(R a, int d) { return __shfl_up_sync(0xffffffffu, a, d); }
   static __device__ __forceinline__ R shfl_xor(R a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
-  // moments
-  static __device__ __forceinline__ A azero() { return 0.0; }
-  static __device__ __forceinline__ A aadd(A s, double x) { return s + x; }
-  static __device__ __forceinline__ double aval(A s, double k) { return s * k; }
   // J from two densities and E
   static __device__ __forceinline__ double flux_J(R r0, R r1, double e, double inv_dx) {
     return (r1 - r0) * inv_dx - e * 0.5 * (r0 + r1);
@@ -80,9 +75,6 @@ struct MP<double> {
 template <>
 struct MP<float> {
   using R = ff;
-  struct A {
-    float s, e;
-  };
   static __device__ __forceinline__ R c(double x) { return ff_from_double(x); }
   static __device__ __forceinline__ R add(R a, R b) { return ff_add(a, b); }
   static __device__ __forceinline__ R sub(R a, R b) { return ff_sub(a, b); }
@@ -94,13 +86,6 @@ struct MP<float> {
   static __device__ __forceinline__ R zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ R shfl_up(R a, int d) { return ff_shfl_up(a, d); }
   static __device__ __forceinline__ R shfl_xor(R a, int m) { return ff_shfl_xor(a, m); }
-  // compensated (two-sum) accumulation of float terms
-  static __device__ __forceinline__ A azero() { return {0.f, 0.f}; }
-  static __device__ __forceinline__ A aadd(A a, float x) {
-    const ff t = two_sum(a.s, x);
-    return {t.hi, __fadd_rn(a.e, t.lo)};
-  }
-  static __device__ __forceinline__ float aval(A a, float k) { return __fmaf_rn(a.s, k, __fmul_rn(a.e, k)); }
   static __device__ __forceinline__ float flux_J(R r0, R r1, float e, float inv_dx) {
     const float dr = ff_sub(r1, r0).hi;
     return dr * inv_dx - e * 0.5f * (r0.hi + r1.hi);
@@ -540,44 +525,27 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
   const float rb_f = (float)rb;  // the criteria's float combination
 
   // Sums of the lane partials of one interface column over each half of the
-  // lane group (negative / positive velocities), by shuffles, with a
-  // compensation term in the FP32 path (two-sum at every level); lane 0 of
-  // the group stores {pos, pos err, neg, neg err} and the norm.  Every
-  // thread calls it with warp-uniform control flow; `valid` only gates the
-  // store.
+  // lane group (negative / positive velocities), by shuffles; lane 0 of the
+  // group stores the flux, the two half moments and the norm.  Plain sums in
+  // the FP32 path too: each lane's partial already carries the rounding of
+  // its products of float g, so compensating the sum over the lanes would
+  // not make the flux more accurate than its inputs.  Every thread calls it
+  // with warp-uniform control flow; `valid` only gates the store.
   auto reduce_store = [&](int i, bool valid, G p, G q) {
-    G pe = G(0);
 #pragma unroll
     for (int m = nhp >> 1; m >= 1; m >>= 1) {
-      const G op = __shfl_xor_sync(0xffffffffu, p, m);
-      if constexpr (sizeof(G) == 4) {
-        const G oe = __shfl_xor_sync(0xffffffffu, pe, m);
-        const ff t = two_sum(p, op);
-        p = t.hi;
-        pe = __fadd_rn(__fadd_rn(pe, oe), t.lo);
-      } else {
-        p += op;
-      }
+      p += __shfl_xor_sync(0xffffffffu, p, m);
       if constexpr (ADAPT) q += __shfl_xor_sync(0xffffffffu, q, m);
     }
     const int src = warp_base + nhp;
     const G pp = __shfl_sync(0xffffffffu, p, src);
-    G ppe = G(0), qq = G(0);
-    if constexpr (sizeof(G) == 4) ppe = __shfl_sync(0xffffffffu, pe, src);
+    G qq = G(0);
     if constexpr (ADAPT) qq = __shfl_sync(0xffffffffu, q, src);
     if (valid && lig == 0) {
-      // pp (+ ppe): <v^+ g>; p (+ pe): sum over the negative velocities
-      if constexpr (sizeof(G) == 4) {
-        const ff t = two_sum(pp, p);  // compensated <v g>
-        const float e = __fadd_rn(__fadd_rn(ppe, pe), t.lo);
-        C.fk[i] = __fmaf_rn(t.hi, g_kflux, __fmul_rn(e, g_kflux));
-        C.mp[i] = __fadd_rn(pp, ppe);
-        C.mm[i] = -__fadd_rn(p, pe);
-      } else {
-        C.fk[i] = (pp + p) * g_kflux;
-        C.mp[i] = pp;
-        C.mm[i] = -p;
-      }
+      // pp: <v^+ g>; p: the sum over the negative velocities
+      C.fk[i] = (pp + p) * g_kflux;
+      C.mp[i] = pp;
+      C.mm[i] = -p;
       if constexpr (ADAPT) C.n2[i] = q + qq;
     }
   };

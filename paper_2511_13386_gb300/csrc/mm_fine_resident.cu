@@ -16,8 +16,8 @@
 //              groups are read (the left one) or copied to a stash (the
 //              right one) before the barrier that precedes the sweep; the
 //              per-lane partial moments <w v g> of the new column are stored;
-//   macro (i)  per cell: the interface flux F = (dt/dx) <xi g>/eps by a
-//              compensated sum of the partials, m+- = <v^+- g>, the warp
+//   macro (i)  per cell: the interface flux F = (dt/dx) <xi g>/eps as the
+//              sum of the partials, m+- = <v^+- g>, the warp
 //              sums of F, and the boundary values the neighbouring warps and
 //              CTAs need; the CTA's first and last new columns are copied
 //              into the neighbouring CTAs' halo buffers;
@@ -38,7 +38,7 @@
 // the streaming kernel).
 //
 // Precision: g, the sweep and the per-lane partials in float; the density
-// and the field in float-float; the flux by compensated summation.
+// and the field in float-float; the flux as a float sum of the partials.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -305,9 +305,11 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   auto macro_i = [&](int p, bool with_flux) {
     if (w < nwc) {
       const float* pp = part + tid;
-      // m-: negative-velocity lanes, m+: positive ones; the total flux by
-      // compensated (two-sum) accumulation in two independent chains
-      float sp = 0.f, sm = 0.f, cs[2] = {0.f, 0.f}, ce[2] = {0.f, 0.f};
+      // m-: negative-velocity lanes, m+: positive ones; the flux is their
+      // sum.  Plain float sums: each lane's partial already carries the
+      // rounding of its eight products of float g, so a compensated sum over
+      // the lanes would not make the flux more accurate than its inputs
+      float sp = 0.f, sm = 0.f;
       float t[LG];
 #pragma unroll
       for (int q = 0; q < LG; ++q) t[q] = pp[q * PS];
@@ -315,15 +317,10 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
       for (int q = 0; q < LG; ++q) {
         if (q >= HALF) sp += t[q];
         else sm += t[q];
-        const ff u = two_sum(cs[q & 1], t[q]);
-        cs[q & 1] = u.hi;
-        ce[q & 1] = __fadd_rn(ce[q & 1], u.lo);
       }
-      const ff tot = two_sum(cs[0], cs[1]);
-      const float err = __fadd_rn(__fadd_rn(ce[0], ce[1]), tot.lo);
       mp = sp;
       mm = -sm;
-      Fc = with_flux ? __fmaf_rn(tot.hi, f_kflux, __fmul_rn(err, f_kflux)) : 0.f;
+      Fc = with_flux ? __fmul_rn(__fadd_rn(sp, sm), f_kflux) : 0.f;
       float ws = Fc;
 #pragma unroll
       for (int m = 16; m > 0; m >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, m);

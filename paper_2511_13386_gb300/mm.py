@@ -27,7 +27,7 @@ STATUS_NAMES = ["MM_OK", "MM_ERR_INVALID", "MM_ERR_OOM", "MM_ERR_CUDA", "MM_ERR_
                 "MM_ERR_UNSTABLE", "MM_ERR_BUSY", "MM_ERR_NOT_READY", "MM_ERR_UNKNOWN_TICKET"]
 
 EXPORTED = ["mm_params_default", "mm_create", "mm_destroy", "mm_query", "mm_fine_propagate",
-            "mm_fine_propagate_noalloc", "mm_autotune", "mm_coarse", "mm_lift", "parareal_run", "mm_coarse_guess",
+            "mm_fine_propagate_noalloc", "mm_autotune", "mm_set_chunk_entry", "mm_coarse", "mm_lift", "parareal_run", "mm_coarse_guess",
             "mm_parareal_correct", "mm_batch_footprint",
             "mm_batch_create", "mm_batch_add", "mm_batch_step", "mm_batch_query", "mm_batch_take",
             "mm_batch_bytes", "mm_batch_counters", "mm_batch_destroy", "parareal_run_many", "mm_server_create", "serve_submit",
@@ -133,6 +133,7 @@ def load(build_if_missing: bool = True):
             "mm_fine_propagate_noalloc": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V,
                                                          V, V, P(mm_fine_stats), V]),
             "mm_autotune": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_int32, V, V, V, V, P(mm_tune_result), V]),
+            "mm_set_chunk_entry": (ctypes.c_int, [V, ctypes.c_double]),
             "mm_coarse": (ctypes.c_int, [V, ctypes.c_int32, ctypes.c_double, V, V, V]),
             "mm_lift": (ctypes.c_int, [V, ctypes.c_int32, V, V, V]),
             "parareal_run": (ctypes.c_int, [V, P(mm_parareal_cfg), V, V, V, P(mm_parareal_stats), V]),
@@ -320,6 +321,10 @@ def mm_query(ctx: Ctx, t_span: float) -> dict:
     info = mm_info()
     _check(load().mm_query(ctx.handle, t_span, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in mm_info._fields_}
+
+
+def mm_set_chunk_entry(ctx: Ctx, entry_steps: float):
+    _check(load().mm_set_chunk_entry(ctx.handle, float(entry_steps)))
 
 
 def mm_fine_propagate(ctx: Ctx, batch: int, t_span: float, rho_in, g_in, rho_out, g_out,

@@ -152,3 +152,37 @@ def test_autotune_measures_the_step_chunk_entry_cost():
         assert rel(ro_h[b], r_ref) <= FP32_TOL
     mm.mm_autotune(ctx, 0, 1, None, None, None, None)
     ctx.close()
+
+
+def test_set_chunk_entry_fixes_the_launch_plan():
+    """mm_set_chunk_entry replaces the measured entry cost in the launch
+    planner: a very high cost runs a batch larger than the GPU holds as one
+    launch of whole states (two waves), a low one in rounds of chunks; both results match the
+    oracle, and out-of-range costs are refused."""
+    dev = device()
+    w = W.batched()
+    B = 160
+    rho, g, r, gg, ro, go = _arrays(w, B, dev)
+    p = params(w.nx, w.nv, w.eps, mm.MM_FP32G, rho_bar=1.0)
+    p.fine_kernel = 2
+    ctx = mm.mm_create(p)
+    mm.mm_autotune(ctx, B, 32, r, gg, ro, go)
+    q = mm.mm_query(ctx, 1.0)
+    span = 200 * q["dt_limit"] * (1 - 1e-9)
+    dt = mm.mm_query(ctx, span)["dt"]
+    op = oparams(p)
+    launches = {}
+    for e in (1.0, 1000.0):
+        mm.mm_set_chunk_entry(ctx, e)
+        st = mm.mm_fine_propagate(ctx, B, span, r, gg, ro, go, stats=True)
+        assert st["device_status"] == 0
+        launches[e] = st["launches"]
+        ro_h = ro.cpu().numpy()
+        for b in (0, B - 1):
+            r_ref, _, _, _ = O.fine(op, 200, dt, rho[b], g[b])
+            assert rel(ro_h[b], r_ref) <= FP32_TOL
+    assert launches[1.0] > launches[1000.0] == 1, launches  # rounds of chunks vs one launch of whole states
+    for bad in (-1.0, 1001.0, float("nan")):
+        with pytest.raises(mm.MMError):
+            mm.mm_set_chunk_entry(ctx, bad)
+    ctx.close()
