@@ -390,6 +390,14 @@ __device__ void lift_block(const FineArgs& A, const double* rho, double rb, G* g
   __syncthreads();
 }
 
+// v[k] = p[k T + threadIdx.x + d] (periodic in nx) for the NR rows of a
+// pass over the cells (see fine_state).
+template <int NR, int T, class V>
+__device__ __forceinline__ void pre_rows(V (&v)[NR], const V* p, int d, int nx) {
+#pragma unroll
+  for (int k = 0; k < NR; ++k) v[k] = p[wrapi(k * T + (int)threadIdx.x + d, nx)];
+}
+
 // F for one state: n_steps steps from (rin, gin); gin == nullptr lifts the
 // density first.  buf0/buf1 are the two step buffers (the last step writes
 // buf0); the column arrays are carved from colsmem (shared memory, up to
@@ -438,6 +446,13 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     return wrapi(c + d, nx);
   };
   constexpr int T = kFineThreads;
+  // Values p[c + d] (periodic) of the cells of every row, read before a pass
+  // over the cells when the rows unroll.  The column arrays that did not fit
+  // shared memory (the field's low part, the end values) are read through
+  // the same kind of pointer as the shared ones, so inside a pass the
+  // compiler keeps each row's read behind the previous row's stores: one L2
+  // round trip per row.  Read first, the rows' reads are in flight together.
+  constexpr int NR = NROW != 0 ? NROW : 1;
 
   double* red = reinterpret_cast<double*>(smem);
   Cols<G> C = carve<G>(colsmem, colglob, nx, ADAPT, budget);
@@ -674,7 +689,15 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         // D2 f = (270 s1 - 27 s2 + 2 s3 - 490 f0) / 180,
         // D3 f = (-13 e1 + 8 e2 - e3) / 8, with e_k = f_{+k} - f_{-k},
         // s_k = f_{+k} + f_{-k} (then divided by dx^d).
-        auto Ef = [&](int c) { return ff{C.par[4 * c], C.elo[c]}; };
+        float elo0[NR], elom[NR];  // the field's low part at c and c - 1
+        if constexpr (NROW != 0) {
+          pre_rows<NR, T>(elo0, C.elo, 0, nx);
+          pre_rows<NR, T>(elom, C.elo, -1, nx);
+        }
+        auto elo_at = [&](int c, int d) {
+          if constexpr (NROW != 0) return d == 0 ? elo0[krow] : elom[krow];
+          else return C.elo[nb(c, d)];
+        };
         ff* Jf = reinterpret_cast<ff*>(C.jd);
         const ff k1 = {A.f_k1, A.f_k1_lo};
         auto rho_f = [&](int c, int d) { return C.rho[nb(c, d)]; };
@@ -684,7 +707,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           const ff e2 = ff_sub_abs(rho_f(c, 2), rho_f(c, -2));
           const ff e3 = ff_sub_abs(rho_f(c, 3), rho_f(c, -3));
           const ff D1 = ff_mul(ff_add_abs(ff_sub_abs(ff_mul_f(e1, 45.f), ff_mul_f(e2, 9.f)), e3), k1);
-          ff Ec = ff_add_abs(Ef(nb(c, -1)), Ef(c));
+          ff Ec = ff_add_abs(ff{C.par[4 * nb(c, -1)], elo_at(c, -1)}, ff{C.par[4 * c], elo_at(c, 0)});
           Ec.hi *= 0.5f;
           Ec.lo *= 0.5f;
           const ff J = ff_sub_abs(D1, ff_mul(Ec, C.rho[c]));
@@ -825,6 +848,12 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
     }
 
     // J and the sweep constants: E+/dv, E-/dv, P = <X>, J
+    float4 ends4[NR];  // FP32, rows unrolled: the end values and the
+    float eloc[NR];    // field's low part of every row, read first
+    if constexpr (F32 && NROW != 0) {
+      pre_rows<NR, T>(ends4, reinterpret_cast<const float4*>(C.ends), 0, nx);
+      pre_rows<NR, T>(eloc, C.elo, 0, nx);
+    }
     cells([&](int c) {
       const int cl = nb(c, -1), cr = nb(c, 1);
       G* pr = C.par + 4 * c;
@@ -833,7 +862,9 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       const G pm = ((C.mp[c] - C.mp[cl]) - (C.mm[cr] - C.mm[c])) * g_inv_dx;
       G en[4];
       if constexpr (sizeof(G) == 4) {
-        const float4 e4 = *reinterpret_cast<const float4*>(C.ends + 4 * c);
+        float4 e4;
+        if constexpr (NROW != 0) e4 = ends4[krow];
+        else e4 = *reinterpret_cast<const float4*>(C.ends + 4 * c);
         en[0] = e4.x; en[1] = e4.y; en[2] = e4.z; en[3] = e4.w;
       } else {
         for (int q = 0; q < 4; ++q) en[q] = C.ends[4 * c + q];
@@ -851,7 +882,10 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         ff avg = ff_add_abs(r0, r1);
         avg.hi *= 0.5f;
         avg.lo *= 0.5f;
-        const ff J = ff_sub_abs(ff_mul_f(ff_sub_abs(r1, r0), g_inv_dx), ff_mul(ff{pr[0], C.elo[c]}, avg));
+        float el;
+        if constexpr (NROW != 0) el = eloc[krow];
+        else el = C.elo[c];
+        const ff J = ff_sub_abs(ff_mul_f(ff_sub_abs(r1, r0), g_inv_dx), ff_mul(ff{pr[0], el}, avg));
         pr[3] = J.hi;
         pr[1] = J.lo;
       } else {
@@ -899,13 +933,18 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       });
       const ff Fbar = ff_mul(block_sum_ff(fsum, red), Rinv_nx);  // (syncs: fluxes visible)
       const ff mdx = {-Rdx.hi, -Rdx.lo};
+      float eloc[NR];  // rows unrolled: the field's low part of every row, read first
+      if constexpr (NROW != 0) pre_rows<NR, T>(eloc, C.elo, 0, nx);
       // sums of terms that are small against the density and the field:
       // the absolute-error form (error ~2^-47 of the operands) suffices
       cells([&](int c) {
         const int cl = nb(c, -1);
         const ff Fl = {C.fk[cl], C.par[4 * cl + 1]}, Fc = {C.fk[c], C.par[4 * c + 1]};
         C.rho[c] = ff_add_abs(C.rho[c], ff_sub_abs(Fl, Fc));
-        const ff E = ff_add_abs(ff{C.par[4 * c], C.elo[c]}, ff_mul(ff_sub_abs(Fc, Fbar), mdx));
+        float el;
+        if constexpr (NROW != 0) el = eloc[krow];
+        else el = C.elo[c];
+        const ff E = ff_add_abs(ff{C.par[4 * c], el}, ff_mul(ff_sub_abs(Fc, Fbar), mdx));
         C.par[4 * c] = E.hi;
         C.elo[c] = E.lo;
       });
