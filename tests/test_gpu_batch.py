@@ -236,3 +236,28 @@ def test_batch_large_grid_sequential_parts_on_a_cluster():
     bound = max(FP64_TOL, 2 * _sensitivity(p, w, t_end, N, K, ref))
     assert rel(outs[0], ref) <= bound, (rel(outs[0], ref), bound)
     assert infos[0]["mass_drift"] <= 1e-12
+
+
+def test_batch_groups_large_solves_by_grid():
+    """Large solves of two grid sizes beside a small one in one batch: the
+    sequential parts run as one cluster launch per grid size (Nx = 16384,
+    two solves; Nx = 32768, one) and one work-list launch for the small
+    solve; every result matches its single-solve run, and each large solve
+    is bitwise the same alone in a batch and in the mix."""
+    specs = [(16384, 16, 1e-2, 4, 2), (256, 32, 1e-2, 5, 3), (32768, 16, 1e-1, 3, 2), (16384, 16, 1e-3, 3, 2)]
+    solves = []
+    for q, (nx, nv, eps, N, K) in enumerate(specs):
+        w = W.batched(nx, nv, eps, seed=W.SEED_BASE + 91 + q, n_slices=N)
+        p = params(nx, nv, eps, mm.MM_FP64, rho_bar=1.0)
+        ctx = mm.mm_create(p)
+        dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+        ctx.close()
+        solves.append((p, w, N * 2 * dt * (1 - 1e-9), N, K))
+    outs, infos, _ = _run_batch(solves)
+    for (p, w, t_end, N, K), o, info in zip(solves, outs, infos):
+        single, sinfo = _single(p, w, t_end, N, K)
+        assert info["iterations"] == sinfo["iterations"] == K
+        assert rel(o, single) <= FP64_TOL, (p.nx, rel(o, single))
+    for q in (0, 2):
+        alone, _, _ = _run_batch([solves[q]])
+        assert np.array_equal(alone[0], outs[q]), q

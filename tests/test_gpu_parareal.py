@@ -279,12 +279,12 @@ def _chain_rounding_spread(op, rho0, span, N, ref, fr=None, want=None):
     return spread
 
 
-@pytest.mark.parametrize("nx", [64, 256, 1024, 2048, 4096, 32768])
+@pytest.mark.parametrize("nx", [64, 256, 1024, 2048, 4096, 8192, 32768])
 def test_coarse_guess_and_correction_entry_points(nx):
     """Algorithm 1's sequential parts through their own entry points (from
     Nx = 256 one solve's implicit step runs over a thread-block cluster,
-    one row per thread up to Nx = 1024 and chunks of 2, 4 and 32 rows per
-    thread beyond; Nx = 64 on one CTA): the coarse guess rho^{n+1,0} = G(rho^{n,0}) over 12 slices and
+    one row per thread up to Nx = 1024 and chunks of 2, 4, 8 and 32 rows
+    per thread beyond; Nx = 64 on one CTA): the coarse guess rho^{n+1,0} = G(rho^{n,0}) over 12 slices and
     one correction sweep rho^{n+1,1} = F + (G(rho^{n,1}) - G(rho^{n,0})),
     against the oracle's G composed slice by slice: at 1e-12, or where the
     chain's conditioning makes correct double-precision evaluations drift
