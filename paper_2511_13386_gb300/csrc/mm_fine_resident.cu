@@ -13,9 +13,9 @@
 //              in place (upwind v d_x g, E d_v g, (I - Pi), relaxation),
 //              from a register ring holding the old columns i-1, i, i+1 and
 //              a prefetch; the old columns it needs from the neighbouring
-//              groups are read (the left one) or copied to a stash (the
-//              right one) before the barrier that precedes the sweep; the
-//              per-lane partial moments <w v g> of the new column are stored;
+//              groups come from stashes that each group fills right after
+//              its sweep of the step before; the per-lane partial moments
+//              <w v g> of the new column are stored;
 //   macro (i)  per cell: the interface flux F = (dt/dx) <xi g>/eps as the
 //              sum of the partials, m+- = <v^+- g>, the warp
 //              sums of F, and the boundary values the neighbouring warps and
@@ -23,7 +23,10 @@
 //              into the neighbouring CTAs' halo buffers;
 //   exchange   one barrier per step (cluster-wide when C > 1); every
 //              exchange buffer is double-buffered by step parity, so one
-//              barrier separates each write from its read and the next write;
+//              barrier separates each write from its read and the next write
+//              (with runs as long as the lane groups are wide, where every
+//              thread's cell is swept by its own warp, that is the step's
+//              only block-wide barrier);
 //   macro (ii) per cell: rho^{n+1} = rho^n + F_{i-1/2} - F_{i+1/2}; the
 //              field by the discrete Ampere identity (below); J, P = <X> and
 //              the sweep constants of the next step.
@@ -70,7 +73,7 @@ constexpr int VPT = 8;  // velocity nodes per lane (two 16-byte chunks)
 // that the groups of a warp, which read the same position of their runs at
 // once, hit different banks.
 struct ResMap {
-  unsigned g, halo, stash, part, par, wfirst, wlast, xch, pro, red, total;
+  unsigned g, halo, stash, stashl, part, par, wfirst, wlast, xch, pro, red, total;
   unsigned xch_stride;  // bytes per parity in xch
 };
 
@@ -82,10 +85,11 @@ __host__ __device__ inline ResMap res_map(int n, int nv, int lanes, int C) {
   m.g = o;      o = up16(o + 4u * n * nv);
   m.halo = o;   o = up16(o + 4u * 4 * nv);          // [parity][left, right][nv]
   m.part = o;   o = up16(o + 4u * (lanes + 4) * (n + 1));  // [lanes + 4][n + 1], see below
-  m.stash = o;  o = up16(o + 4u * (T / lanes) * nv);  // per group: next group's old first column
+  m.stash = o;  o = up16(o + 4u * 2 * (T / lanes) * nv);  // [parity][group]: next group's old first column
+  m.stashl = o; o = up16(o + 4u * 2 * NW * nv);       // [parity][warp]: previous warp's old last column
   m.par = o;    o = up16(o + 16u * (n + n / ((unsigned)n / (T / lanes))));  // padded, see below
-  m.wfirst = o; o = up16(o + 16u * NW);             // per warp: F, m-, rho.hi, rho.lo
-  m.wlast = o;  o = up16(o + 16u * NW);             // per warp: F, m+
+  m.wfirst = o; o = up16(o + 2 * 16u * NW);         // [parity][warp]: F, m-, rho.hi, rho.lo
+  m.wlast = o;  o = up16(o + 2 * 16u * NW);         // [parity][warp]: F, m+
   m.xch_stride = up16(16u + 4u * C * NW);           // xL(F, m+), xR(F, m-), sums
   m.xch = o;    o = up16(o + 2u * m.xch_stride);
   m.pro = o;    o = up16(o + 32u * C);              // entry exchange, per rank
@@ -166,6 +170,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   float* halo = reinterpret_cast<float*>(smem + Mp.halo);
   float* part = reinterpret_cast<float*>(smem + Mp.part);
   float* stash = reinterpret_cast<float*>(smem + Mp.stash);
+  float* stashl = reinterpret_cast<float*>(smem + Mp.stashl);
   float* par = reinterpret_cast<float*>(smem + Mp.par);
   float* wfirst = reinterpret_cast<float*>(smem + Mp.wfirst);
   float* wlast = reinterpret_cast<float*>(smem + Mp.wlast);
@@ -326,13 +331,13 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
       for (int m = 16; m > 0; m >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, m);
       float* X = xch(p);
       if (lane == 0) {
-        st4(wfirst + 4 * w, make_float4(Fc, mm, rho.hi, rho.lo));
+        st4(wfirst + 4 * (p * NW + w), make_float4(Fc, mm, rho.hi, rho.lo));
         if (C > 1)
           for (int q = 0; q < C; ++q) remote(X, q)[4 + r * NW + w] = ws;
         else
           X[4 + w] = ws;
       }
-      if (lane == 31) *reinterpret_cast<float2*>(wlast + 4 * w) = make_float2(Fc, mp);
+      if (lane == 31) *reinterpret_cast<float2*>(wlast + 4 * (p * NW + w)) = make_float2(Fc, mp);
       if (C > 1 && tid == 0) *reinterpret_cast<float2*>(remote(X, rl) + 2) = make_float2(Fc, mm);
       if (C > 1 && tid == n - 1) *reinterpret_cast<float2*>(remote(X, rr)) = make_float2(Fc, mp);
     }
@@ -373,15 +378,15 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
     ff rr_old = ff_shfl_down(rho, 1);
     if (lane == 0) {
       float2 v;
-      if (w > 0) v = *reinterpret_cast<const float2*>(wlast + 4 * (w - 1));
+      if (w > 0) v = *reinterpret_cast<const float2*>(wlast + 4 * (p * NW + w - 1));
       else if (C > 1) v = *reinterpret_cast<const float2*>(X);
-      else v = *reinterpret_cast<const float2*>(wlast + 4 * (nwc - 1));
+      else v = *reinterpret_cast<const float2*>(wlast + 4 * (p * NW + nwc - 1));
       Fl = v.x;
       mpl = v.y;
     }
     if (lane == 31) {
       if (w < nwc - 1 || C == 1) {
-        const float4 v = ld4(wfirst + 4 * (w < nwc - 1 ? w + 1 : 0));
+        const float4 v = ld4(wfirst + 4 * (p * NW + (w < nwc - 1 ? w + 1 : 0)));
         Fr = v.x;
         mmr = v.y;
         rr_old = {v.z, v.w};
@@ -422,23 +427,49 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   // registers of the ring: P = old column i-1, Q = i, N = i+1, F = i+2
   float R0[VPT], R1[VPT], R2[VPT], R3[VPT];
 
-  // old first column of the next group: the stash (filled by that group
-  // before the barrier), or the right halo for the CTA's last group
+  // The neighbouring groups' old columns a sweep needs, by parity p of the
+  // step that produced them: the next group's first column (right stash,
+  // read at the end of the run, after that group has overwritten it), and,
+  // for the first group of a warp, the previous group's last column (left
+  // stash: that group belongs to another warp, which may already be
+  // sweeping).  Every group writes its entries right after its sweep, before
+  // the step's cluster (or block) barrier, which orders them for the
+  // readers; the two parities keep the next step's writes off the entries
+  // still being read.
+  constexpr int GPW = 32 / LG;  // lane groups per warp
+  auto stash_r = [&](int p, int gr) { return stash + (unsigned)(p * NGRP + gr) * nv; };
+  auto stash_l = [&](int p, int wq) { return stashl + (unsigned)(p * NW + wq) * nv; };
+  auto stash_write = [&](int p) {
+    const float* c0 = col(i0);
+    float* d = stash_r(p, grp == 0 ? NGRP - 1 : grp - 1);
+    st4(d + ch0, ld4(c0 + ch0));
+    st4(d + ch1, ld4(c0 + ch1));
+    const int gn = grp + 1 == NGRP ? 0 : grp + 1;
+    if (gn % GPW == 0) {
+      const float* cl = col(i0 + R - 1);
+      float* e = stash_l(p, gn / GPW);
+      st4(e + ch0, ld4(cl + ch0));
+      st4(e + ch1, ld4(cl + ch1));
+    }
+  };
+  // old first column of the next group: the right stash, or the right halo
+  // for the CTA's last group
   auto right_next = [&](int p) -> const float* {
     if (C > 1 && grp == NGRP - 1) return halo + (unsigned)(2 * p + 1) * nv;
-    return stash + (unsigned)grp * nv;
+    return stash_r(p, grp);
   };
-  // before the barrier that precedes the sweep: the ring's first columns,
-  // and this group's old first column into the previous group's stash
+  // the ring's first columns: the previous group's last column (in this
+  // warp: read directly, that group has not started its sweep; else the
+  // left stash, or the left halo for the CTA's first group) and this
+  // group's first three
   auto preload = [&](int p) {
-    const float* lc = i0 > 0 ? col(i0 - 1) : (C > 1 ? halo + (unsigned)(2 * p) * nv : col(n - 1));
+    const float* lc;
+    if (i0 > 0) lc = grp % GPW != 0 ? col(i0 - 1) : stash_l(p, grp / GPW);
+    else lc = C > 1 ? halo + (unsigned)(2 * p) * nv : stash_l(p, 0);
     ldcol(R0, lc);
     ldcol(R1, col(i0));
     ldcol(R2, col(i0 + 1));
     ldcol(R3, col(i0 + 2));
-    float* sd = stash + (unsigned)(grp == 0 ? NGRP - 1 : grp - 1) * nv;
-    st4(sd + ch0, make_float4(R1[0], R1[1], R1[2], R1[3]));
-    st4(sd + ch1, make_float4(R1[4], R1[5], R1[6], R1[7]));
   };
 
   auto sweep = [&](int p) {
@@ -493,6 +524,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   };
 
   // ------------------------------------------------------------ step loop --
+  stash_write(0);  // g^0 (the block barrier after the partials of g^0 made every column visible)
   macro_i(0, false);
   cluster_or_block_sync(C);
   macro_ii(0, false, true);
@@ -501,6 +533,7 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
   for (int64_t s = 0; s < A.n_steps; ++s) {
     const int pc = (int)(s & 1), pn = pc ^ 1;  // this step's buffers, the next step's
     sweep(pc);
+    stash_write(pn);
     // when every group's run is as long as the group is wide, thread t owns
     // cell t, which its own group swept: the partials it sums are the
     // group's (a warp barrier suffices) and the warps run on into macro (i)
@@ -512,7 +545,10 @@ __global__ void __launch_bounds__(T, 2) fine_resident_kernel(const FineArgs A, i
     const bool last = s + 1 == A.n_steps;
     macro_ii(pn, true, !last);
     if (!last) preload(pn);
-    __syncthreads();
+    // when warp-local, everything the next sweep reads from other warps went
+    // through the cluster (or block) barrier above; the exit after the last
+    // step reads every column
+    if (!warp_local || last) __syncthreads();
   }
 
   // -------------------------------------------------------------- exit ---
