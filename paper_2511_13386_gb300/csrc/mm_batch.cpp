@@ -48,6 +48,7 @@ struct mm_batch {
   int device = 0;
   int n_sm = 0;
   int max_ctas = 0;  // cap on the work-list launch's CTAs (0: one per SM)
+  int cluster_min_nx = 4096;  // sequential parts of solves from this grid on run over a cluster
   uint64_t next_id = 1;
   std::map<uint64_t, std::unique_ptr<Solve>> solves;
   size_t bytes_in_use = 0;
@@ -171,24 +172,27 @@ extern "C" mm_status mm_batch_add(mm_batch* b, const mm_params* p, const mm_para
 }
 
 // One parareal iteration of every unfinished solve.
-// Grids from which a solve's sequential parts (coarse guess, correction)
-// run over a thread-block cluster, one cluster of 8 SMs per solve, instead
-// of one CTA: there the one-CTA step is bound by its SM's FP64 pipe (0.7 ms
-// per step at Nx = 32768).  Below them a batch's many solves keep every
-// SM's FP64 pipe busy with one CTA each, which does less work per step in
-// total than the cluster layout.
-constexpr int kClusterMinNx = 16384;
-
-static bool on_cluster(const mmk::CorrectArgs& c) { return c.m.nx >= kClusterMinNx && mmk::coarse_cluster_ok(c.m); }
+// A solve's sequential parts (coarse guess, correction) run over a
+// thread-block cluster, one cluster of 8 SMs per solve, from the batch's
+// cluster_min_nx on, else on one CTA.  The one-CTA step is bound by its
+// SM's FP64 pipe (about 0.3 ms per step at Nx = 8192, 0.7 ms at 32768), and
+// the longest such chain sets the length of a step's correction launch; the
+// cluster step does about as much work per step in total from Nx = 4096 on,
+// in a fraction of the time.  A batch that shares the GPU with another (the
+// server's two lanes) keeps the clusters for the largest grids: a cluster
+// needs 8 free SMs of one GPC, which the other batch's launches may hold.
+static bool on_cluster(const mmk::CorrectArgs& c, int min_nx) {
+  return c.m.nx >= min_nx && mmk::coarse_cluster_ok(c.m);
+}
 
 // Orders `ca` for launch_sequential: the one-CTA entries first, then the
 // cluster entries grouped by grid size; returns the one-CTA count.
-static int order_sequential(std::vector<mmk::CorrectArgs>& ca) {
-  std::stable_sort(ca.begin(), ca.end(), [](const mmk::CorrectArgs& x, const mmk::CorrectArgs& y) {
-    return (on_cluster(x) ? x.m.nx : 0) < (on_cluster(y) ? y.m.nx : 0);
+static int order_sequential(std::vector<mmk::CorrectArgs>& ca, int min_nx) {
+  std::stable_sort(ca.begin(), ca.end(), [min_nx](const mmk::CorrectArgs& x, const mmk::CorrectArgs& y) {
+    return (on_cluster(x, min_nx) ? x.m.nx : 0) < (on_cluster(y, min_nx) ? y.m.nx : 0);
   });
   int n = 0;
-  while (n < (int)ca.size() && !on_cluster(ca[n])) ++n;
+  while (n < (int)ca.size() && !on_cluster(ca[n], min_nx)) ++n;
   return n;
 }
 
@@ -247,7 +251,7 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
       ca.push_back(c);
       v->started = true;
     }
-    const int n_small = order_sequential(ca);
+    const int n_small = order_sequential(ca, b->cluster_min_nx);
     e = cudaMemcpyAsync(d_corr, ca.data(), sizeof(mmk::CorrectArgs) * ca.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_sequential(ca, d_corr, n_small, true, nx_max, (double*)b->macro_ws.p, s);
     if (e != cudaSuccess) return mm_cuda_fail(e, "batch: coarse guess");
@@ -353,7 +357,7 @@ extern "C" mm_status mm_batch_step(mm_batch* b, int32_t* active_out, void* strea
     c.err = d_err + q;
     ca.push_back(c);
   }
-  const int n_small = order_sequential(ca);
+  const int n_small = order_sequential(ca, b->cluster_min_nx);
   e = cudaMemcpyAsync(d_corr, ca.data(), sizeof(mmk::CorrectArgs) * ca.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_sequential(ca, d_corr, n_small, false, nx_max, (double*)b->macro_ws.p, s);
   if (e != cudaSuccess) return mm_cuda_fail(e, "batch: corrections");
@@ -473,4 +477,8 @@ extern "C" mm_status parareal_run_many(int32_t n, const mm_params* params, const
 
 void mmk::batch_set_max_ctas(mm_batch* b, int n) {
   if (b) b->max_ctas = n > 0 ? n : 0;
+}
+
+void mmk::batch_set_cluster_min_nx(mm_batch* b, int nx) {
+  if (b) b->cluster_min_nx = nx;
 }

@@ -258,6 +258,11 @@ double solve_iteration_cost(const mm_params& p, const mm_parareal_cfg& c);
 // Cap on the CTAs of a batch's work-list launch (0: one per SM); lets two
 // batches share the GPU on disjoint SMs.
 void batch_set_max_ctas(mm_batch* b, int n);
+// Grid from which a batch runs a solve's coarse guess and correction over a
+// thread-block cluster instead of one CTA (4096 unless set).
+void batch_set_cluster_min_nx(mm_batch* b, int nx);
+// The server's lanes share the GPU: clusters only for the largest grids.
+constexpr int kServeClusterMinNx = 16384;
 double ctx_mean(const double* rho, int nx);
 
 }  // namespace mmk

@@ -133,8 +133,10 @@ struct mm_server {
         else inflight[j->batch_id] = j;
       }
       if (inflight.empty()) continue;
-      if (bst == MM_OK)
+      if (bst == MM_OK) {
         mmk::batch_set_max_ctas(batch, lane == 1 ? n_sm - reserve : (long_resident.load() > 0 ? reserve : n_sm));
+        mmk::batch_set_cluster_min_nx(batch, mmk::kServeClusterMinNx);
+      }
       int32_t active = 0;
       mm_status st = mm_batch_step(batch, &active, s);
       if (st != MM_OK) {  // the round failed: every resident solve fails with it

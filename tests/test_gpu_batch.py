@@ -238,6 +238,39 @@ def test_batch_large_grid_sequential_parts_on_a_cluster():
     assert infos[0]["mass_drift"] <= 1e-12
 
 
+def test_batch_mid_size_grids_sequential_parts_on_a_cluster():
+    """A batch that has the GPU to itself runs the coarse guess and the
+    corrections of its solves of Nx >= 4096 over a thread-block cluster, one
+    launch per grid size after the one-CTA launch of the smaller solves:
+    every result matches its single-solve run (which takes the cluster
+    layout at every supported grid), each mid-size solve is bitwise the same
+    alone and in the mix, and the Nx = 4096 solve matches the oracle within
+    the rounding spread of its implicit steps."""
+    specs = [(4096, 16, 1e-2, 4, 2), (1024, 16, 1e-2, 5, 2), (8192, 16, 1e-1, 3, 2)]
+    solves = []
+    for q, (nx, nv, eps, N, K) in enumerate(specs):
+        w = W.batched(nx, nv, eps, seed=W.SEED_BASE + 131 + q, n_slices=N)
+        p = params(nx, nv, eps, mm.MM_FP64, rho_bar=1.0)
+        ctx = mm.mm_create(p)
+        dt = mm.mm_query(ctx, 1.0)["dt_limit"]
+        ctx.close()
+        solves.append((p, w, N * 2 * dt * (1 - 1e-9), N, K))
+    outs, infos, _ = _run_batch(solves)
+    for (p, w, t_end, N, K), o, info in zip(solves, outs, infos):
+        single, sinfo = _single(p, w, t_end, N, K)
+        assert info["iterations"] == sinfo["iterations"] == K
+        assert rel(o, single) <= FP64_TOL, (p.nx, rel(o, single))
+        assert info["mass_drift"] <= 1e-12
+    for q in (0, 2):
+        alone, _, _ = _run_batch([solves[q]])
+        assert np.array_equal(alone[0], outs[q]), q
+    p, w, t_end, N, K = solves[0]
+    ref, _, it = O.parareal(oparams(p), w.rho0, w.g0, t_end, N, K)
+    assert it == K
+    bound = max(FP64_TOL, 2 * _sensitivity(p, w, t_end, N, K, ref))
+    assert rel(outs[0], ref) <= bound, (rel(outs[0], ref), bound)
+
+
 def test_batch_groups_large_solves_by_grid():
     """Large solves of two grid sizes beside a small one in one batch: the
     sequential parts run as one cluster launch per grid size (Nx = 16384,
