@@ -177,10 +177,12 @@ extern "C" mm_status mm_batch_add(mm_batch* b, const mm_params* p, const mm_para
 // cluster_min_nx on, else on one CTA.  The one-CTA step is bound by its
 // SM's FP64 pipe (about 0.3 ms per step at Nx = 8192, 0.7 ms at 32768), and
 // the longest such chain sets the length of a step's correction launch; the
-// cluster step does about as much work per step in total from Nx = 4096 on,
-// in a fraction of the time.  A batch that shares the GPU with another (the
-// server's two lanes) keeps the clusters for the largest grids: a cluster
-// needs 8 free SMs of one GPC, which the other batch's launches may hold.
+// cluster step shortens that chain several-fold (57 us against 0.7 ms at
+// Nx = 32768) for 8 SMs per solve while it runs.  On small grids it costs
+// far more SM time than one CTA (at Nx = 1024, 10.9 us on 8 SMs against
+// 19 us on one).  A batch that shares the GPU with another (the server's two
+// lanes) keeps the clusters for the largest grids: a cluster needs 8 free
+// SMs of one GPC, which the other batch's launches may hold.
 static bool on_cluster(const mmk::CorrectArgs& c, int min_nx) {
   return c.m.nx >= min_nx && mmk::coarse_cluster_ok(c.m);
 }
