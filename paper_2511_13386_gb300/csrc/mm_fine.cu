@@ -41,6 +41,27 @@
 
 namespace mmk {
 
+// Unnormalised float-float forms for the inside of a stencil: the pair
+// (s, w) that the sloppy addition of ff.cuh holds before its final Fast2Sum,
+// and the product by a float before its Fast2Sum.  |w| may exceed
+// ulp(s)/2, and after a cancellation s may carry none of the value, so only
+// another unnormalised or sloppy operation or a double-word product may read
+// such a pair; the absolute error stays the sloppy addition's, about 2^-47
+// of the operands.
+__device__ __forceinline__ ff ff_add_raw(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ ff ff_sub_raw(ff a, ff b) {
+  const ff s = two_sum(a.hi, -b.hi);
+  return {s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ ff ff_mul_f_raw(ff a, float b) {
+  const float ch = __fmul_rn(a.hi, b);
+  const float cl = __fmaf_rn(a.hi, b, -ch);
+  return {ch, __fmaf_rn(a.lo, b, cl)};
+}
+
 // Table 1 (Sec. 2.2), offsets -3..3, rows = derivative order 1..3.
 __constant__ double kFD[3][7] = {
     {-1.0 / 60, 3.0 / 20, -3.0 / 4, 0.0, 3.0 / 4, -3.0 / 20, 1.0 / 60},
@@ -688,7 +709,9 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         // applied with integer weights: D1 f = (45 e1 - 9 e2 + e3) / 60,
         // D2 f = (270 s1 - 27 s2 + 2 s3 - 490 f0) / 180,
         // D3 f = (-13 e1 + 8 e2 - e3) / 8, with e_k = f_{+k} - f_{-k},
-        // s_k = f_{+k} + f_{-k} (then divided by dx^d).
+        // s_k = f_{+k} + f_{-k} (then divided by dx^d).  Inside a stencil the
+        // pairs stay unnormalised (ff_*_raw); the last operation before a
+        // high part is read alone normalises.
         float elo0[NR], elom[NR];  // the field's low part at c and c - 1
         if constexpr (NROW != 0) {
           pre_rows<NR, T>(elo0, C.elo, 0, nx);
@@ -703,11 +726,11 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         auto rho_f = [&](int c, int d) { return C.rho[nb(c, d)]; };
         ff jsum = {0.f, 0.f};
         cells([&](int c) {
-          const ff e1 = ff_sub_abs(rho_f(c, 1), rho_f(c, -1));
-          const ff e2 = ff_sub_abs(rho_f(c, 2), rho_f(c, -2));
-          const ff e3 = ff_sub_abs(rho_f(c, 3), rho_f(c, -3));
-          const ff D1 = ff_mul(ff_add_abs(ff_sub_abs(ff_mul_f(e1, 45.f), ff_mul_f(e2, 9.f)), e3), k1);
-          ff Ec = ff_add_abs(ff{C.par[4 * nb(c, -1)], elo_at(c, -1)}, ff{C.par[4 * c], elo_at(c, 0)});
+          const ff e1 = ff_sub_raw(rho_f(c, 1), rho_f(c, -1));
+          const ff e2 = ff_sub_raw(rho_f(c, 2), rho_f(c, -2));
+          const ff e3 = ff_sub_raw(rho_f(c, 3), rho_f(c, -3));
+          const ff D1 = ff_mul(ff_add_raw(ff_sub_raw(ff_mul_f_raw(e1, 45.f), ff_mul_f_raw(e2, 9.f)), e3), k1);
+          ff Ec = ff_add_raw(ff{C.par[4 * nb(c, -1)], elo_at(c, -1)}, ff{C.par[4 * c], elo_at(c, 0)});
           Ec.hi *= 0.5f;
           Ec.lo *= 0.5f;
           const ff J = ff_sub_abs(D1, ff_mul(Ec, C.rho[c]));
@@ -723,10 +746,11 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           const ff Jm2 = Jf[nb(c, -2)], Jp2 = Jf[nb(c, 2)];
           const ff Jm3 = Jf[nb(c, -3)], Jp3 = Jf[nb(c, 3)];
           const ff e1 = ff_sub_abs(Jp1, Jm1), e2 = ff_sub_abs(Jp2, Jm2), e3 = ff_sub_abs(Jp3, Jm3);
-          const ff s1 = ff_add_abs(Jp1, Jm1), s2 = ff_add_abs(Jp2, Jm2), s3 = ff_add_abs(Jp3, Jm3);
-          const ff n3 = ff_sub_abs(ff_add_abs(ff_mul_f(e1, -13.f), ff_mul_f(e2, 8.f)), e3);
-          const ff n2 = ff_add_abs(ff_add_abs(ff_mul_f(s1, 270.f), ff_mul_f(s2, -27.f)),
-                                   ff_add_abs(ff_mul_f(s3, 2.f), ff_mul_f(J0, -490.f)));
+          // (e_k stay normalised: their high parts form D1 J in float below)
+          const ff s1 = ff_add_raw(Jp1, Jm1), s2 = ff_add_raw(Jp2, Jm2), s3 = ff_add_raw(Jp3, Jm3);
+          const ff n3 = ff_sub_abs(ff_add_raw(ff_mul_f_raw(e1, -13.f), ff_mul_f_raw(e2, 8.f)), e3);
+          const ff n2 = ff_add_abs(ff_add_raw(ff_mul_f_raw(s1, 270.f), ff_mul_f_raw(s2, -27.f)),
+                                   ff_add_raw(ff_mul_f_raw(s3, 2.f), ff_mul_f_raw(J0, -490.f)));
           const float d3J = n3.hi * A.f_k3;
           const float d2J = n2.hi * A.f_k2;
           const float d1J = (45.f * e1.hi - 9.f * e2.hi + e3.hi) * A.f_k1;
