@@ -736,7 +736,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
           const ff J = ff_sub_abs(D1, ff_mul(Ec, C.rho[c]));
           C.par[4 * c + 2] = D1.hi;  // d rho / dx for the second pass
           Jf[c] = J;
-          jsum = ff_add_abs(jsum, J);
+          jsum = ff_add_raw(jsum, J);  // (the block sum normalises)
         });
         const float meanJ = block_sum_ff(jsum, red).hi * A.f_inv_nx;  // (syncs: Jc visible)
         const float rbf = rb_f;
@@ -903,13 +903,13 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         // high part (slot 3); the low part replaces the field's (slot 1,
         // dead after the criteria).
         const ff r0 = C.rho[c], r1 = C.rho[cr];
-        ff avg = ff_add_abs(r0, r1);
+        ff avg = ff_add_raw(r0, r1);  // (read only by the product below)
         avg.hi *= 0.5f;
         avg.lo *= 0.5f;
         float el;
         if constexpr (NROW != 0) el = eloc[krow];
         else el = C.elo[c];
-        const ff J = ff_sub_abs(ff_mul_f(ff_sub_abs(r1, r0), g_inv_dx), ff_mul(ff{pr[0], el}, avg));
+        const ff J = ff_sub_abs(ff_mul_f_raw(ff_sub_raw(r1, r0), g_inv_dx), ff_mul(ff{pr[0], el}, avg));
         pr[3] = J.hi;
         pr[1] = J.lo;
       } else {
@@ -953,7 +953,7 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
         const ff F = is_kin(c) ? flux_kin(c) : flux_fluid(c);
         C.fk[c] = F.hi;
         C.par[4 * c + 1] = F.lo;
-        fsum = ff_add_abs(fsum, F);
+        fsum = ff_add_raw(fsum, F);  // (the block sum normalises)
       });
       const ff Fbar = ff_mul(block_sum_ff(fsum, red), Rinv_nx);  // (syncs: fluxes visible)
       const ff mdx = {-Rdx.hi, -Rdx.lo};
@@ -964,11 +964,11 @@ __device__ __forceinline__ void fine_state(const FineArgs& A, const double* rin,
       cells([&](int c) {
         const int cl = nb(c, -1);
         const ff Fl = {C.fk[cl], C.par[4 * cl + 1]}, Fc = {C.fk[c], C.par[4 * c + 1]};
-        C.rho[c] = ff_add_abs(C.rho[c], ff_sub_abs(Fl, Fc));
+        C.rho[c] = ff_add_abs(C.rho[c], ff_sub_raw(Fl, Fc));
         float el;
         if constexpr (NROW != 0) el = eloc[krow];
         else el = C.elo[c];
-        const ff E = ff_add_abs(ff{C.par[4 * c], el}, ff_mul(ff_sub_abs(Fc, Fbar), mdx));
+        const ff E = ff_add_abs(ff{C.par[4 * c], el}, ff_mul(ff_sub_raw(Fc, Fbar), mdx));
         C.par[4 * c] = E.hi;
         C.elo[c] = E.lo;
       });
