@@ -411,12 +411,16 @@ MM_API mm_status mm_parareal_correct(mm_ctx* ctx, int32_t n_slices, int32_t k, d
 
 /* A batch of independent parareal solves (Algorithm 1, Sec. 3.3) of any
    shapes, advanced together: each mm_batch_step runs one parareal iteration
-   of every unfinished solve in three launches -- the coarse guess of newly
-   added solves (one CTA per solve), every fine propagation F the iteration
-   needs, of all solves and slices, as one work list walked by a persistent
-   kernel (longest items first; each item lifts its slice density in place,
-   so no per-slice perturbation is stored), and the sequential corrections
-   with their successive errors (one CTA per solve).  Solves may be added
+   of every unfinished solve in a few launches whatever the number of
+   solves -- the coarse guess of newly added solves, every fine propagation
+   F the iteration needs, of all solves and slices, as one work list walked
+   by a persistent kernel (longest items first; each item lifts its slice
+   density in place, so no per-slice perturbation is stored), and the
+   sequential corrections with their successive errors.  The coarse guess
+   and the corrections run on one CTA per solve, and over a thread-block
+   cluster of 8 CTAs for a solve of nx >= 4096 (a power of two up to 32768;
+   one launch per grid size): its chain of implicit coarse steps is then
+   several times shorter.  Solves may be added
    between steps; a finished solve stays until taken.  The F of a batch is
    the streaming kernel (FP32 g with 8 velocity nodes per lane, or FP64 with
    4: nv / 16, resp. nv / 8, a whole number of lanes, at most 32 lanes).
@@ -499,7 +503,10 @@ typedef struct {
    others to the short lane; the long lane's launches leave one eighth of
    the SMs to the short lane, so small requests do not wait behind rounds of
    large ones (the short lane uses every SM while no long solve is
-   resident).  A request's footprint is mm_batch_footprint plus its share of
+   resident).  The lanes' batches keep the cluster layout of the coarse guess
+   and corrections for nx >= 16384: a cluster needs 8 free SMs of one GPC,
+   which the other lane's launches may hold.  A request's footprint is
+   mm_batch_footprint plus its share of
    the fine kernel's step buffers (two states per SM) plus 1 MiB.  Requests
    that arrive while others run join their lane at its next round; a result
    does not depend on the requests it ran with.  If a round fails, the
