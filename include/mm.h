@@ -78,9 +78,11 @@ typedef enum {
 
 typedef enum {
   MM_FP64 = 0,   /* g stored and updated in double; every sum in double */
-  MM_FP32G = 1   /* g stored and updated in float; density, Poisson solve,
-                    moment combination and mass kept in compensated
-                    float-float (~48-bit) arithmetic, output density double */
+  MM_FP32G = 1   /* g stored and updated in float, its velocity moments
+                    summed in float; density, field (Poisson law), fluid
+                    flux and the criteria's stencils in float-float (~48-bit)
+                    arithmetic, so mass is kept to float-float rounding;
+                    output density double */
 } mm_precision;
 
 /* Optional device-memory callbacks (e.g. a framework's caching allocator). */
