@@ -188,8 +188,13 @@ MM_API mm_status mm_query(const mm_ctx* ctx, double t_span, mm_info* out);
 
 /* F over a span (Sec. 2.3, eq. S^HMM; eq. S^MM when adapt == 0):
    n = ceil(t_span / dt_limit) steps of size t_span / n for every state of
-   the batch, all states in one launch.  Per step and state: the Poisson law
-   of S^MM for E, the flux J of S^0, the criteria of Sec. 2.2 and the status
+   the batch, all states in one launch (the resident kernel: in rounds of
+   step chunks when the batch exceeds the clusters the GPU holds at once;
+   stats->launches counts them).  Per step and state: the Poisson law of
+   S^MM for E (in the FP32 path with one flux per interface, solved at entry
+   and then advanced by the discrete Ampere identity it implies under the
+   flux-form density update), the flux J of S^0, the criteria of Sec. 2.2
+   and the status
    update of Sec. 2.3 (adapt == 1), the g update on kinetic interfaces
    (upwind transport, (I - Pi) projection, field term, exponential
    relaxation), g = 0 on fluid interfaces, and the density update.
