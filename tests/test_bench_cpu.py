@@ -29,3 +29,36 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_profiled_traffic_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
+    """`roofline.traffic` comes from a committed ncu summary only while the
+    kernel's sources hash to the value the summary records; a stale or
+    missing summary gives null, never another kernel's bytes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "kernel.cu"
+    src.write_text("__global__ void k() {}\n")
+    prof = tmp_path / "summary.md"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.PROFILES, "resident", (str(prof), ["kernel.cu"]))
+    assert bench.profiled_traffic("resident") is None  # no summary
+    h = bench.kernel_source_hash("resident")
+    prof.write_text(f"# k\n\ntraffic_bytes_per_launch: 123456\nkernel_source_sha256: {h}\n")
+    assert bench.profiled_traffic("resident") == 123456
+    src.write_text("__global__ void k() { }\n")  # the kernel changed since the capture
+    assert bench.profiled_traffic("resident") is None
+
+
+def test_committed_summaries_carry_traffic_and_a_source_hash():
+    """Every summary the bench reads names its DRAM bytes per launch and the
+    hash of the sources it was taken on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for kind, (path, files) in bench.PROFILES.items():
+        text = open(path).read()
+        fields = dict(ln.split(":", 1) for ln in text.splitlines()
+                      if ln.startswith(("traffic_bytes_per_launch:", "kernel_source_sha256:")))
+        assert int(fields["traffic_bytes_per_launch"]) > 0, kind
+        assert len(fields["kernel_source_sha256"].strip()) == 64, kind
+        assert all(os.path.exists(os.path.join(ROOT, f)) for f in files), kind
